@@ -1,0 +1,478 @@
+"""FP64 CPU oracle of the speckle-masking reconstruction path.
+
+TEST INFRASTRUCTURE ONLY.  This module is imported by ``tests/``, by
+``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py``;
+the product path (the CUDA library and its Python binding) never imports,
+links or runs it, and it imports nothing from the product.
+
+It is a plain, slow, obviously correct restatement of what the paper
+computes, in float64 numpy, one function per step.  The paper (Li et al.,
+"High Performance Parallel Image Reconstruction for New Vacuum Solar
+Telescope") names the steps but prints only Eq. 1; every other formula is
+the standard one of the methods it cites (Labeyrie 1970 for the modulus;
+Weigelt 1977 and Lohmann, Weigelt & Wirnitzer 1983 for the bispectrum and
+the recursive phase).  Where the paper is silent the reading taken here is
+stated in each docstring:
+
+* subfield grid (Sect. 2, Sect. 3.2): stride N/2, ``ceil((W-N)/s)+1`` tiles
+  per axis, edge tiles keep their true extent and are zero-padded to N x N;
+* apodisation (silent): separable Tukey window, taper ``t`` px per edge;
+* DFT (Sect. 2): centred frequencies k in [-N/2, N/2) of the windowed,
+  mean-subtracted tile, each frame divided by its windowed flux, DC := 1;
+* power and mean spectrum (Sect. 3.2, Eq. 1 numerator), noise floor as the
+  mean power in the half-plane corners of the (2K+1)^2 box outside the disk;
+* bispectrum (Sect. 2, Sect. 3.2; Weigelt 1977) on the pair domain
+  D = {u in upper half plane, |u| <= r, 0 < |v| <= R, |u+v| <= r};
+* modulus (Sect. 3.2, Eq. 1) with a model STF (Sect. 3.2), filtered by the
+  diffraction OTF T0;
+* recursive phase (Sect. 3.2; LWW 1983), rings of equal |w|^2, anchors from
+  the burst-mean spectrum, |B| weighting by default;
+* inverse DFT, flux rescale and the mean restored under the window
+  (Sect. 2, Sect. 3.2), mosaic as
+  sum(rec) / sum(window) (Sect. 3.2, the merge step).
+
+Parity of every function here is pinned by ``tests/test_oracle_pins.py``
+against brute force, closed forms, invariants and library routines.
+Model-STF fidelity to real seeing (the Korff constant) is parity unpinned:
+the paper prints no STF model.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+W_BISPEC = 0     # phasor terms weighted by |B| (the plain sum of B's phasors)
+W_UNIT = 1       # unit-modulus phasor terms
+
+
+# ----------------------------------------------------------------------------
+# subfields and window (Sect. 2: partially overlapping subimage cubes)
+# ----------------------------------------------------------------------------
+def subfield_grid(W: int, H: int, N: int, stride: int) -> List[Tuple[int, int, int, int]]:
+    """Overlapping subfields (x0, y0, w, h), row-major over y then x.
+
+    The paper cuts each frame into partially overlapping cubes matching the
+    isoplanatic patch (Sect. 2, Sect. 3.2).  Reading: tiles start every
+    ``stride`` px; a ragged last tile keeps its true extent ``w, h < N``.
+    """
+    def starts(L: int) -> List[int]:
+        n = 1 if L <= N else int(math.ceil((L - N) / stride)) + 1
+        return [k * stride for k in range(n)]
+
+    out = []
+    for y0 in starts(H):
+        for x0 in starts(W):
+            out.append((x0, y0, min(N, W - x0), min(N, H - y0)))
+    return out
+
+
+def tukey(L: int, taper: int) -> np.ndarray:
+    """1-D window of length L: raised-cosine ramps of ``taper`` px at both ends.
+
+    Ramp value at pixel x is (1 - cos(pi (x + 1/2) / taper)) / 2 for
+    x < taper, 1 beyond; the window is the smaller of the rising ramp read
+    from each end, so it is symmetric and strictly positive.  taper = 0
+    gives all ones (no apodisation).
+    """
+    x = np.arange(L, dtype=np.float64)
+    if taper <= 0:
+        return np.ones(L)
+
+    def ramp(p: np.ndarray) -> np.ndarray:
+        return np.where(p < taper, 0.5 * (1.0 - np.cos(np.pi * (p + 0.5) / taper)), 1.0)
+
+    return np.minimum(ramp(x), ramp(L - 1 - x))
+
+
+def window2d(w: int, h: int, taper: int) -> np.ndarray:
+    """Separable apodisation window [h, w]."""
+    return np.outer(tukey(h, taper), tukey(w, taper))
+
+
+# ----------------------------------------------------------------------------
+# DFT (Sect. 2: Fourier transform of every subimage)
+# ----------------------------------------------------------------------------
+def dft_matrix(N: int, sign: int = -1) -> np.ndarray:
+    """E[k + N/2, x] = exp(sign * 2 pi i k x / N) for k in [-N/2, N/2)."""
+    k = np.arange(-(N // 2), N - N // 2, dtype=np.float64)
+    x = np.arange(N, dtype=np.float64)
+    return np.exp(sign * 2j * np.pi * np.outer(k, x) / N)
+
+
+def dft2(t: np.ndarray) -> np.ndarray:
+    """I[ky + N/2, kx + N/2] = sum_{y,x} t[y, x] exp(-2 pi i (kx x + ky y) / N).
+
+    Separable: the x sums (rows) then the y sums (columns), each as a
+    product with the DFT matrix.
+    """
+    N = t.shape[0]
+    E = dft_matrix(N, -1)
+    rows = t @ E.T           # [y, kx]
+    return E @ rows          # [ky, kx]
+
+
+def idft2(I: np.ndarray) -> np.ndarray:
+    """Inverse of dft2: (1/N^2) sum_k I(k) exp(+2 pi i k.x / N), complex [y, x]."""
+    N = I.shape[0]
+    E = dft_matrix(N, +1)    # [k, x]
+    return (E.T @ I @ E) / (N * N)
+
+
+def frame_spectra(frames: np.ndarray, sub: Tuple[int, int, int, int], N: int,
+                  taper: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Normalised spectra of one subfield's frames.
+
+    For frame i the tile of extent w x h at (x0, y0) has windowed mean
+    mu_i = sum(w raw_i) / sum(w); the tile w (raw_i - mu_i) is zero-padded to
+    N x N at the low corner and transformed, and the spectrum is divided by
+    the frame's windowed flux f_i = mu_i sum(w).  The DC value is then set to
+    1 (the normalised mean).  Subtracting the mean before the transform keeps
+    the window's own spectrum, scaled by the bright background, out of the
+    object's spectrum (reading; the paper names no apodisation).
+    Returns (In [F, N, N] complex128 centred, flux [F], mu [F]).
+    """
+    x0, y0, w, h = sub
+    win = window2d(w, h, taper)
+    F = frames.shape[0]
+    In = np.empty((F, N, N), dtype=np.complex128)
+    flux = np.empty(F)
+    mu = np.empty(F)
+    for i in range(F):
+        raw = frames[i, y0:y0 + h, x0:x0 + w].astype(np.float64)
+        mu[i] = (win * raw).sum() / win.sum()
+        flux[i] = mu[i] * win.sum()
+        t = np.zeros((N, N))
+        t[:h, :w] = win * (raw - mu[i])
+        In[i] = dft2(t) / flux[i]
+        In[i, N // 2, N // 2] = 1.0
+    return In, flux, mu
+
+
+# ----------------------------------------------------------------------------
+# frequency domains
+# ----------------------------------------------------------------------------
+def cutoff_radius(N: int, fc: float) -> float:
+    """Radius of the frequency disk U in frequency pixels (fc in cycles/px)."""
+    return fc * N
+
+
+def in_half_plane(kx: np.ndarray, ky: np.ndarray) -> np.ndarray:
+    """Upper half plane used to store one of each Hermitian pair."""
+    return (ky > 0) | ((ky == 0) & (kx > 0))
+
+
+def domain_U(N: int, fc: float) -> np.ndarray:
+    """All (kx, ky) with kx^2 + ky^2 <= r^2, r = fc N.  int64 [n, 2]."""
+    r = cutoff_radius(N, fc)
+    K = int(math.floor(r))
+    ky, kx = np.mgrid[-K:K + 1, -K:K + 1]
+    m = kx * kx + ky * ky <= r * r
+    return np.stack([kx[m], ky[m]], axis=1).astype(np.int64)
+
+
+def domain_V(R: int) -> np.ndarray:
+    """Bispectrum offsets 0 < |v| <= R.  int64 [n, 2]."""
+    ky, kx = np.mgrid[-R:R + 1, -R:R + 1]
+    m = (kx * kx + ky * ky <= R * R) & ((kx != 0) | (ky != 0))
+    return np.stack([kx[m], ky[m]], axis=1).astype(np.int64)
+
+
+def pair_domain(N: int, fc: float, R: int) -> np.ndarray:
+    """Pair domain D of the stored bispectrum, int64 [n, 4] = (ux, uy, vx, vy).
+
+    u in the upper half plane with |u| <= r, v with 0 < |v| <= R and
+    |u + v| <= r.  The rest of the bispectrum follows from
+    B(-u, -v) = conj B(u, v) (real frames).
+    """
+    r2 = cutoff_radius(N, fc) ** 2
+    U = domain_U(N, fc)
+    U = U[in_half_plane(U[:, 0], U[:, 1])]
+    V = domain_V(R)
+    ux = np.repeat(U[:, 0], len(V))
+    uy = np.repeat(U[:, 1], len(V))
+    vx = np.tile(V[:, 0], len(U))
+    vy = np.tile(V[:, 1], len(U))
+    m = (ux + vx) ** 2 + (uy + vy) ** 2 <= r2
+    return np.stack([ux[m], uy[m], vx[m], vy[m]], axis=1)
+
+
+# ----------------------------------------------------------------------------
+# power spectrum, mean spectrum, noise (Sect. 3.2, Eq. 1 numerator)
+# ----------------------------------------------------------------------------
+def power_mean(In: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """P = <|I_i|^2>_i and M = <I_i>_i on the full centred grid (Eq. 1 numerator)."""
+    P = np.mean((In * In.conj()).real, axis=0)
+    M = np.mean(In, axis=0)
+    return P, M
+
+
+def noise_floor(P: np.ndarray, N: int, fc: float) -> float:
+    """Mean of P over {1 <= ky <= K, |kx| <= K, |k| > r}, K = floor(r).
+
+    The optics pass nothing beyond r, so the power there is the flat
+    additive-noise bias; by Hermitian symmetry the upper corners of the
+    (2K+1)^2 box stand for all four.  (Reading; the paper gives no noise
+    treatment.)
+    """
+    r = cutoff_radius(N, fc)
+    K = int(math.floor(r))
+    ky, kx = np.mgrid[1:K + 1, -K:K + 1]
+    m = kx * kx + ky * ky > r * r
+    if not m.any():
+        return 0.0
+    return float(P[ky[m] + N // 2, kx[m] + N // 2].mean())
+
+
+# ----------------------------------------------------------------------------
+# bispectrum (Sect. 2 and Sect. 3.2: speckle masking, Weigelt 1977)
+# ----------------------------------------------------------------------------
+def bispectrum(In: np.ndarray, pairs: np.ndarray) -> np.ndarray:
+    """B(u, v) = (1/F) sum_i I_i(u) I_i(v) conj I_i(u + v) for each listed pair.
+
+    ``In`` is [F, N, N] centred; ``pairs`` rows are (ux, uy, vx, vy).  A
+    direct sum over frames, one frame at a time.
+    """
+    F, N, _ = In.shape
+    c = N // 2
+    ux, uy, vx, vy = (pairs[:, j] for j in range(4))
+    B = np.zeros(len(pairs), dtype=np.complex128)
+    for i in range(F):
+        S = In[i]
+        B += S[uy + c, ux + c] * S[vy + c, vx + c] * np.conj(S[uy + vy + c, ux + vx + c])
+    return B / F
+
+
+# ----------------------------------------------------------------------------
+# modulus (Sect. 3.2, Eq. 1)
+# ----------------------------------------------------------------------------
+def otf_t0(N: int, fc: float) -> np.ndarray:
+    """Diffraction OTF of a circular pupil on the centred N x N grid.
+
+    T0(rho) = (2/pi)(acos rho - rho sqrt(1 - rho^2)) for rho = |k| / r <= 1.
+    """
+    r = cutoff_radius(N, fc)
+    k = np.arange(-(N // 2), N - N // 2, dtype=np.float64)
+    rho = np.hypot(k[None, :], k[:, None]) / r
+    out = np.zeros((N, N))
+    m = rho <= 1.0
+    p = rho[m]
+    out[m] = (2.0 / np.pi) * (np.arccos(p) - p * np.sqrt(1.0 - p * p))
+    return out
+
+
+def stf_model(N: int, fc: float, d_over_r0: Sequence[float], ck: float = 0.435) -> np.ndarray:
+    """Model speckle transfer function on the centred grid (Sect. 3.2).
+
+    Per frame, T0^2 exp(-6.88 (rho D/r0)^(5/3)) + ck (r0/D)^2 T0 (the
+    long-exposure term squared plus the Korff speckle term); averaged over
+    the frames and divided by its value at k = 0.  The paper calibrates a
+    model STF with r0 but prints no model: the form and ``ck`` are readings
+    (parity unpinned against real seeing).
+    """
+    r = cutoff_radius(N, fc)
+    k = np.arange(-(N // 2), N - N // 2, dtype=np.float64)
+    rho = np.hypot(k[None, :], k[:, None]) / r
+    T0 = otf_t0(N, fc)
+    acc = np.zeros((N, N))
+    for d in d_over_r0:
+        acc += T0 * T0 * np.exp(-6.88 * (rho * d) ** (5.0 / 3.0)) + ck * T0 / (d * d)
+    acc /= len(d_over_r0)
+    return acc / acc[N // 2, N // 2]
+
+
+def amplitude(P: np.ndarray, noise: float, stf: np.ndarray, N: int, fc: float) -> np.ndarray:
+    """Object modulus |O| from Eq. 1, noise-debiased and T0-filtered.
+
+    A(u) = sqrt(max(P - noise, 0) / max(STF, 1e-4)) * T0(u) on U, 0 outside,
+    A(0) = 1.  Eq. 1 gives |O|^2 = <|I|^2> / STF; the 1e-4 floor and the T0
+    filter are conditioning readings (the paper is silent on both).
+    """
+    T0 = otf_t0(N, fc)
+    A = np.sqrt(np.maximum(P - noise, 0.0) / np.maximum(stf, 1e-4)) * T0
+    A[T0 <= 0] = 0.0
+    A[N // 2, N // 2] = 1.0
+    return A
+
+
+# ----------------------------------------------------------------------------
+# recursive phase (Sect. 3.2: speckle masking phase, LWW 1983)
+# ----------------------------------------------------------------------------
+class _PairIndex:
+    """Lookup (u, v) -> row of the stored pair list (u must be in the half plane)."""
+
+    def __init__(self, pairs: np.ndarray, K: int, R: int):
+        self.K, self.R = K, R
+        self.keys = self._key(pairs[:, 0], pairs[:, 1], pairs[:, 2], pairs[:, 3])
+        self.order = np.argsort(self.keys)
+        self.sorted = self.keys[self.order]
+
+    def _key(self, ux, uy, vx, vy):
+        K, R = self.K, self.R
+        return (((uy + K) * (2 * K + 1) + (ux + K)) * (2 * R + 1) + (vy + R)) * (2 * R + 1) + (vx + R)
+
+    def find(self, ux, uy, vx, vy) -> np.ndarray:
+        key = self._key(ux, uy, vx, vy)
+        pos = np.searchsorted(self.sorted, key)
+        pos = np.minimum(pos, len(self.sorted) - 1)
+        if not np.all(self.sorted[pos] == key):
+            raise KeyError("pair outside the stored domain")
+        return self.order[pos]
+
+
+def recursion_rings(N: int, fc: float) -> List[np.ndarray]:
+    """Points w of the half-plane disk with |w|^2 >= 2, grouped by |w|^2 ascending."""
+    U = domain_U(N, fc)
+    U = U[in_half_plane(U[:, 0], U[:, 1])]
+    n2 = U[:, 0] ** 2 + U[:, 1] ** 2
+    U = U[n2 >= 2]
+    n2 = n2[n2 >= 2]
+    rings = []
+    for q in np.unique(n2):
+        rings.append(U[n2 == q])
+    return rings
+
+
+def phase_recursion(B: np.ndarray, pairs: np.ndarray, M: np.ndarray, N: int, fc: float,
+                    R: int, weight: int = W_BISPEC) -> np.ndarray:
+    """Unit phasors z(k) = exp(i phi(k)) of the object on the centred grid.
+
+    Speckle masking (Sect. 2, Sect. 3.2): arg B(u, v) = phi(u) + phi(v) -
+    phi(u + v), so every split w = u + v with u and v already known gives an
+    estimate of phi(w).  Reading (the paper gives no details):
+
+    * anchors phi(0) = 0, phi(e_x) = arg M(e_x), phi(e_y) = arg M(e_y), so
+      the result is registered to the burst-mean image;
+    * w runs over the half-plane disk in rings of equal |w|^2, ascending;
+    * the phasor of w sums exp(i(phi(u) + phi(v))) conj B(u, v) over
+      v with 0 < |v| <= R, u = w - v, |u|^2 < |w|^2, |v|^2 < |w|^2, reading
+      B(u, v) = conj B(-u, -v) when u is in the lower half plane;
+      ``W_UNIT`` divides each term by |B| (terms with B = 0 dropped);
+    * z(w) = phasor / |phasor|, and z(w) = 1 when the phasor is 0;
+    * z(-w) = conj z(w).
+    """
+    r = cutoff_radius(N, fc)
+    K = int(math.floor(r))
+    c = N // 2
+    idx = _PairIndex(pairs, K, R)
+    z = np.zeros((N, N), dtype=np.complex128)
+    known = np.zeros((N, N), dtype=bool)
+
+    def setz(kx, ky, val):
+        z[ky + c, kx + c] = val
+        z[-ky + c, -kx + c] = np.conj(val)
+        known[ky + c, kx + c] = True
+        known[-ky + c, -kx + c] = True
+
+    setz(0, 0, 1.0 + 0j)
+    for (ax, ay) in ((1, 0), (0, 1)):
+        m = M[ay + c, ax + c]
+        setz(ax, ay, m / abs(m) if abs(m) > 0 else 1.0 + 0j)
+
+    V = domain_V(R)
+    v2 = V[:, 0] ** 2 + V[:, 1] ** 2
+    for ring in recursion_rings(N, fc):
+        vals = []
+        for (wx, wy) in ring:
+            w2 = wx * wx + wy * wy
+            ux = wx - V[:, 0]
+            uy = wy - V[:, 1]
+            ok = (ux * ux + uy * uy < w2) & (v2 < w2)
+            ux, uy = ux[ok], uy[ok]
+            vx, vy = V[ok, 0], V[ok, 1]
+            upper = in_half_plane(ux, uy)
+            b = np.empty(len(ux), dtype=np.complex128)
+            if upper.any():
+                b[upper] = B[idx.find(ux[upper], uy[upper], vx[upper], vy[upper])]
+            lo = ~upper
+            if lo.any():
+                b[lo] = np.conj(B[idx.find(-ux[lo], -uy[lo], -vx[lo], -vy[lo])])
+            if not (known[uy + c, ux + c].all() and known[vy + c, vx + c].all()):
+                raise AssertionError("recursion used an unknown phase")
+            terms = z[uy + c, ux + c] * z[vy + c, vx + c] * np.conj(b)
+            if weight == W_UNIT:
+                mag = np.abs(b)
+                keep = mag > 0
+                terms = terms[keep] / mag[keep]
+            s = terms.sum()
+            vals.append(s / abs(s) if abs(s) > 0 else 1.0 + 0j)
+        for (wx, wy), val in zip(ring, vals):
+            setz(int(wx), int(wy), val)
+    return z
+
+
+# ----------------------------------------------------------------------------
+# inverse transform and mosaic (Sect. 2, Sect. 3.2)
+# ----------------------------------------------------------------------------
+def inverse(A: np.ndarray, z: np.ndarray, flux_mean: float, mu_mean: float,
+            win: np.ndarray) -> np.ndarray:
+    """Sub-image on the N x N grid (Sect. 2: inverse transform of modulus and phase).
+
+    The non-DC part is Re IDFT(A z) times the burst-mean flux; the mean
+    removed before the transform comes back as mu_mean times the window, so
+    rec is the apodised sub-image.  ``win`` is the [h, w] window, placed at
+    the low corner.
+    """
+    N = A.shape[0]
+    X = A * z
+    X[N // 2, N // 2] = 0.0
+    rec = idft2(X).real * flux_mean
+    h, w = win.shape
+    rec[:h, :w] += mu_mean * win
+    return rec
+
+
+def mosaic(recs: Sequence[np.ndarray], subs: Sequence[Tuple[int, int, int, int]], W: int,
+           H: int, taper: int, min_weight: float = 0.25) -> Tuple[np.ndarray, np.ndarray]:
+    """Merge sub-images: out = sum_s rec_s / sum_s window_s (Sect. 3.2 merge step).
+
+    Each rec_s carries its subfield's window (it is the transform of
+    apodised data), so dividing by the summed windows undoes the
+    apodisation.  Pixels whose summed window is below ``min_weight`` are
+    marked invalid and set to 0 (reading).
+    """
+    num = np.zeros((H, W))
+    den = np.zeros((H, W))
+    for rec, (x0, y0, w, h) in zip(recs, subs):
+        num[y0:y0 + h, x0:x0 + w] += rec[:h, :w]
+        den[y0:y0 + h, x0:x0 + w] += window2d(w, h, taper)
+    valid = den >= min_weight
+    out = np.where(valid, num / np.where(valid, den, 1.0), 0.0)
+    return out, valid
+
+
+# ----------------------------------------------------------------------------
+# whole path
+# ----------------------------------------------------------------------------
+def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: int,
+                         fc: float, R: int, taper: int, stf: np.ndarray,
+                         weight: int = W_BISPEC, pairs: Optional[np.ndarray] = None) -> Dict:
+    """All steps for one subfield; returns every intermediate."""
+    In, flux, mu = frame_spectra(frames, sub, N, taper)
+    P, M = power_mean(In)
+    noise = noise_floor(P, N, fc)
+    if pairs is None:
+        pairs = pair_domain(N, fc, R)
+    B = bispectrum(In, pairs)
+    A = amplitude(P, noise, stf, N, fc)
+    z = phase_recursion(B, pairs, M, N, fc, R, weight)
+    rec = inverse(A, z, float(flux.mean()), float(mu.mean()), window2d(sub[2], sub[3], taper))
+    return {"In": In, "flux": flux, "mu": mu, "P": P, "M": M, "noise": noise, "pairs": pairs,
+            "B": B, "A": A, "z": z, "rec": rec}
+
+
+def reconstruct_burst(frames: np.ndarray, N: int, stride: int, fc: float, R: int, taper: int,
+                      stf: np.ndarray, weight: int = W_BISPEC,
+                      subfields: Optional[Sequence[int]] = None) -> Dict:
+    """Whole burst: every subfield (or the listed ones), then the mosaic."""
+    F, H, W = frames.shape
+    subs = subfield_grid(W, H, N, stride)
+    pairs = pair_domain(N, fc, R)
+    pick = range(len(subs)) if subfields is None else subfields
+    results = {s: reconstruct_subfield(frames, subs[s], N, fc, R, taper, stf, weight, pairs)
+               for s in pick}
+    out = valid = None
+    if subfields is None:
+        out, valid = mosaic([results[s]["rec"] for s in range(len(subs))], subs, W, H, taper)
+    return {"subs": subs, "pairs": pairs, "sub": results, "out": out, "valid": valid}

@@ -1,0 +1,341 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test ties one oracle function to brute force, a closed form, an
+invariant, a library routine or a hand-worked case, so that a dropped term, a
+wrong sign or index, or a transposed operand fails here.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import speckle_oracle as O
+from synth import burst as S
+
+FC = 0.2885
+
+
+# --------------------------------------------------------------------------- grid / window
+def test_subfield_grid_counts():
+    # 1024 / 128 at stride 64: (1024-128)/64 = 14 -> 15 per axis, all full tiles
+    g = O.subfield_grid(1024, 1024, 128, 64)
+    assert len(g) == 225 and all(w == 128 and h == 128 for _, _, w, h in g)
+    # 2560 x 2160 / 256 at stride 128: 19 x 16, last row starts at 1920 with h = 240
+    g = O.subfield_grid(2560, 2160, 256, 128)
+    assert len(g) == 304
+    assert g[-1] == (2304, 1920, 256, 240)
+    assert sum(1 for s in g if s[3] == 240) == 19
+    # a single subfield equal to the frame
+    assert O.subfield_grid(64, 64, 64, 32) == [(0, 0, 64, 64)]
+    # ragged both ways: 200 x 150 / 64 / 32 -> x0 in 0..160 (6), y0 in 0..96 (4)
+    g = O.subfield_grid(200, 150, 64, 32)
+    assert len(g) == 24 and g[5] == (160, 0, 40, 64) and g[-1] == (160, 96, 40, 54)
+
+
+def test_tukey_closed_form():
+    w = O.tukey(16, 4)
+    # (1 - cos(pi/8)) / 2 = 0.0380602337443566 at the first pixel
+    assert w[0] == pytest.approx(0.0380602337443566, abs=1e-15)
+    # (1 - cos(3 pi/8)) / 2 = 0.3086582838174551
+    assert w[1] == pytest.approx(0.3086582838174551, abs=1e-15)
+    assert np.all(w[4:12] == 1.0)
+    assert np.allclose(w, w[::-1])
+    assert np.all(O.tukey(10, 0) == 1.0)
+
+
+# --------------------------------------------------------------------------- DFT
+def test_dft_bruteforce_8x8():
+    rng = np.random.default_rng(1)
+    t = rng.standard_normal((8, 8))
+    I = O.dft2(t)
+    for ky in range(-4, 4):
+        for kx in range(-4, 4):
+            s = 0j
+            for y in range(8):
+                for x in range(8):
+                    s += t[y, x] * complex(math.cos(-2 * math.pi * (kx * x + ky * y) / 8),
+                                           math.sin(-2 * math.pi * (kx * x + ky * y) / 8))
+            assert abs(I[ky + 4, kx + 4] - s) < 1e-12
+
+
+def test_dft_matches_library_fft_and_inverse():
+    rng = np.random.default_rng(2)
+    t = rng.standard_normal((32, 32))
+    I = O.dft2(t)
+    ref = np.fft.fftshift(np.fft.fft2(t))
+    assert np.max(np.abs(I - ref)) < 1e-11
+    assert np.max(np.abs(O.idft2(I).real - t)) < 1e-12
+
+
+def test_dft_parseval():
+    rng = np.random.default_rng(3)
+    t = rng.standard_normal((16, 16))
+    I = O.dft2(t)
+    assert np.sum(np.abs(I) ** 2) == pytest.approx(256 * np.sum(t * t), rel=1e-12)
+
+
+def test_dft_gaussian_closed_form():
+    N, sig, c = 64, 3.0, 32.0
+    y, x = np.mgrid[0:N, 0:N]
+    g = np.exp(-((x - c) ** 2 + (y - c) ** 2) / (2 * sig * sig))
+    I = O.dft2(g)
+    k = np.arange(-32, 32)
+    kx, ky = np.meshgrid(k, k)
+    f2 = (kx ** 2 + ky ** 2) / N ** 2
+    closed = 2 * np.pi * sig ** 2 * np.exp(-2 * np.pi ** 2 * sig ** 2 * f2) \
+        * np.exp(-2j * np.pi * (kx + ky) * c / N)
+    assert np.max(np.abs(I - closed)) < 1e-10
+
+
+# --------------------------------------------------------------------------- spectra, P, M
+def _circular_frames(N, F, seed, dr0=6.0, psf="kolmogorov"):
+    """Noise-free periodic frames: object circularly convolved with each PSF."""
+    rng = np.random.default_rng(seed)
+    obj = S.make_object(N, N, rng)
+    psfs = []
+    frames = np.empty((F, N, N))
+    for i in range(F):
+        p = S.diffraction_psf(N, FC) if psf == "diffraction" else S.kolmogorov_psf(N, dr0, rng, FC)
+        psfs.append(p)
+        frames[i] = np.real(np.fft.ifft2(np.fft.fft2(obj) * np.fft.fft2(p)))
+    return obj, np.array(psfs), frames
+
+
+def test_spectra_normalisation_and_window_mean():
+    rng = np.random.default_rng(4)
+    frames = 1.0 + rng.random((3, 40, 50))
+    In, flux, mu = O.frame_spectra(frames, (5, 3, 30, 28), 32, 4)
+    win = O.window2d(30, 28, 4)
+    for i in range(3):
+        raw = frames[i, 3:31, 5:35]
+        assert flux[i] == pytest.approx((win * raw).sum(), rel=1e-13)
+        assert mu[i] == pytest.approx((win * raw).sum() / win.sum(), rel=1e-13)
+        assert In[i, 16, 16] == 1.0
+        # Hermitian: real tile
+        assert np.max(np.abs(In[i, 1:, 1:] - np.conj(In[i, 1:, 1:][::-1, ::-1]))) < 1e-14
+
+
+def test_power_spectrum_equals_object_times_empirical_stf():
+    """Circular frames, no window, no noise: P = |O/O(0)|^2 <|H|^2> off DC (Eq. 1)."""
+    N, F = 32, 6
+    obj, psfs, frames = _circular_frames(N, F, 5)
+    In, flux, mu = O.frame_spectra(frames, (0, 0, N, N), N, 0)
+    P, M = O.power_mean(In)
+    On = np.fft.fftshift(np.fft.fft2(obj)) / obj.sum()
+    stf = S.empirical_stf(psfs)
+    exp = np.abs(On) ** 2 * stf
+    exp[N // 2, N // 2] = 1.0
+    assert np.max(np.abs(P - exp)) < 1e-14
+    assert P[N // 2, N // 2] == 1.0
+    otf = np.fft.fftshift(np.fft.fft2(psfs, axes=(-2, -1)), axes=(-2, -1))
+    Mexp = On * otf.mean(axis=0)
+    Mexp[N // 2, N // 2] = 1.0
+    assert np.max(np.abs(M - Mexp)) < 1e-14
+
+
+def test_noise_floor_region():
+    N = 64
+    P = np.zeros((N, N))
+    r = FC * N
+    K = int(r)
+    k = np.arange(-32, 32)
+    kx, ky = np.meshgrid(k, k)
+    corner = (ky >= 1) & (ky <= K) & (np.abs(kx) <= K) & (kx ** 2 + ky ** 2 > r * r)
+    P[corner] = 3.0
+    P[~corner] = 100.0
+    assert O.noise_floor(P, N, FC) == 3.0
+
+
+# --------------------------------------------------------------------------- bispectrum
+def test_pair_domain_bruteforce_small():
+    N, fc, R = 8, math.sqrt(5) / 8, 2
+    D = O.pair_domain(N, fc, R)
+    brute = []
+    for uy in range(-4, 5):
+        for ux in range(-4, 5):
+            if not (uy > 0 or (uy == 0 and ux > 0)) or ux * ux + uy * uy > 5:
+                continue
+            for vy in range(-R, R + 1):
+                for vx in range(-R, R + 1):
+                    if (vx, vy) == (0, 0) or vx * vx + vy * vy > R * R:
+                        continue
+                    if (ux + vx) ** 2 + (uy + vy) ** 2 <= 5:
+                        brute.append((ux, uy, vx, vy))
+    assert sorted(map(tuple, D.tolist())) == sorted(brute)
+    assert len(O.domain_U(N, fc)) == 21 and len(brute) == 76
+
+
+def test_bispectrum_translation_invariance():
+    N, F = 32, 4
+    _, _, frames = _circular_frames(N, F, 6)
+    pairs = O.pair_domain(N, FC, 4)
+    In, _, _ = O.frame_spectra(frames, (0, 0, N, N), N, 0)
+    Is, _, _ = O.frame_spectra(np.roll(frames, (5, -3), axis=(1, 2)), (0, 0, N, N), N, 0)
+    assert np.max(np.abs(O.bispectrum(In, pairs) - O.bispectrum(Is, pairs))) < 1e-12
+
+
+def test_bispectrum_exchange_symmetry():
+    N, F = 32, 3
+    _, _, frames = _circular_frames(N, F, 7)
+    In, _, _ = O.frame_spectra(frames, (0, 0, N, N), N, 4)
+    pairs = O.pair_domain(N, FC, 4)
+    B = O.bispectrum(In, pairs)
+    swapped = pairs[:, [2, 3, 0, 1]]
+    ok = O.in_half_plane(swapped[:, 0], swapped[:, 1])
+    Bs = O.bispectrum(In, swapped[ok])
+    assert ok.sum() > 20
+    assert np.max(np.abs(B[ok] - Bs)) < 1e-15
+
+
+def test_bispectrum_point_source():
+    N, a = 16, 2.5
+    t = np.zeros((N, N))
+    t[5, 11] = a
+    I = O.dft2(t)[None]
+    pairs = O.pair_domain(N, 0.4, 3)
+    B = O.bispectrum(I, pairs)
+    assert np.max(np.abs(B - a ** 3)) < 1e-12
+    # B(u, 0) = I(0) |I(u)|^2 on a random spectrum
+    rng = np.random.default_rng(8)
+    I2 = O.dft2(rng.standard_normal((N, N)))[None]
+    p0 = np.array([[1, 2, 0, 0], [3, 0, 0, 0]])
+    B0 = O.bispectrum(I2, p0)
+    for j, (ux, uy, _, _) in enumerate(p0):
+        assert B0[j] == pytest.approx(I2[0, 8, 8] * abs(I2[0, uy + 8, ux + 8]) ** 2, rel=1e-12)
+
+
+# --------------------------------------------------------------------------- STF / amplitude
+def test_otf_t0_closed_form_points():
+    N = 64
+    T0 = O.otf_t0(N, 0.25)           # r = 16 frequency px
+    assert T0[32, 32] == 1.0
+    # rho = 0.5: (2/pi)(pi/3 - sqrt(3)/4) = 0.3910022189557706
+    assert T0[32, 40] == pytest.approx(0.3910022189557706, abs=1e-15)
+    assert T0[32, 48] == 0.0 and T0[32, 49] == 0.0
+
+
+def test_stf_model_closed_form():
+    N = 64
+    stf = O.stf_model(N, 0.25, [4.0], ck=0.0)
+    # rho = 0.5, D/r0 = 4: T0^2 exp(-6.88 * 2^(5/3)) = 0.152882735... * 3.8238e-10
+    exp = 0.3910022189557706 ** 2 * math.exp(-6.88 * 2.0 ** (5.0 / 3.0))
+    assert stf[32, 40] == pytest.approx(exp, rel=1e-12)
+    stf2 = O.stf_model(N, 0.25, [4.0, 8.0], ck=0.5)
+    t0 = 0.3910022189557706
+    num = (t0 ** 2 * math.exp(-6.88 * 2.0 ** (5 / 3)) + 0.5 * t0 / 16
+           + t0 ** 2 * math.exp(-6.88 * 4.0 ** (5 / 3)) + 0.5 * t0 / 64) / 2
+    den = (1 + 0.5 / 16 + 1 + 0.5 / 64) / 2
+    assert stf2[32, 40] == pytest.approx(num / den, rel=1e-12)
+    assert stf2[32, 32] == 1.0
+
+
+def test_amplitude_with_empirical_stf_is_object_modulus():
+    """Noise-free circular frames, empirical STF: A = |O/O(0)| T0 (Eq. 1)."""
+    N, F = 32, 5
+    obj, psfs, frames = _circular_frames(N, F, 9)
+    In, _, _ = O.frame_spectra(frames, (0, 0, N, N), N, 0)
+    P, _ = O.power_mean(In)
+    stf = S.empirical_stf(psfs)
+    A = O.amplitude(P, 0.0, stf, N, FC)
+    On = np.abs(np.fft.fftshift(np.fft.fft2(obj))) / obj.sum()
+    T0 = O.otf_t0(N, FC)
+    m = (stf > 1e-4) & (T0 > 0)
+    m[N // 2, N // 2] = False
+    assert np.max(np.abs(A[m] - On[m] * T0[m])) < 1e-12
+    assert A[N // 2, N // 2] == 1.0
+    assert np.all(A[T0 == 0] == 0)
+
+
+# --------------------------------------------------------------------------- recursion
+def test_recursion_rings_small():
+    rings = O.recursion_rings(8, math.sqrt(5) / 8)
+    got = [sorted(map(tuple, r.tolist())) for r in rings]
+    assert got == [[(-1, 1), (1, 1)], [(0, 2), (2, 0)], [(-2, 1), (-1, 2), (1, 2), (2, 1)]]
+
+
+def test_recursion_hand_worked_8x8():
+    """R = 1 chain on 8x8 with arbitrary B, checked against hand-derived sums."""
+    N, fc, R = 8, math.sqrt(5) / 8, 1
+    pairs = O.pair_domain(N, fc, R)
+    rng = np.random.default_rng(10)
+    B = rng.standard_normal(len(pairs)) + 1j * rng.standard_normal(len(pairs))
+    M = np.zeros((N, N), complex)
+    M[4, 5] = np.exp(0.3j) * 0.7      # (1, 0)
+    M[5, 4] = np.exp(-1.1j) * 0.4     # (0, 1)
+    z = O.phase_recursion(B, pairs, M, N, fc, R)
+
+    def b(ux, uy, vx, vy):
+        j = [i for i, p in enumerate(pairs.tolist()) if p == [ux, uy, vx, vy]]
+        return B[j[0]]
+
+    z10, z01 = np.exp(0.3j), np.exp(-1.1j)
+    # w = (1, 1): splits (u, v) = ((0,1),(1,0)) and ((1,0),(0,1))
+    s = z01 * z10 * np.conj(b(0, 1, 1, 0)) + z10 * z01 * np.conj(b(1, 0, 0, 1))
+    assert z[5, 5] == pytest.approx(s / abs(s), abs=1e-14)
+    z11 = s / abs(s)
+    # w = (-1, 1): v = (-1,0), u = (0,1); v = (0,1), u = (-1,0) -> conj B((1,0),(0,-1))
+    zm10 = np.conj(z10)
+    s = z01 * zm10 * np.conj(b(0, 1, -1, 0)) + zm10 * z01 * b(1, 0, 0, -1)
+    assert z[5, 3] == pytest.approx(s / abs(s), abs=1e-14)
+    # w = (2, 0): only u = v = (1, 0)
+    s = z10 * z10 * np.conj(b(1, 0, 1, 0))
+    assert z[4, 6] == pytest.approx(s / abs(s), abs=1e-14)
+    # w = (2, 1): v = (1,0) -> u = (1,1); v = (0,1) -> u = (2,0)
+    z20 = s / abs(s)
+    s = z11 * z10 * np.conj(b(1, 1, 1, 0)) + z20 * z01 * np.conj(b(2, 0, 0, 1))
+    assert z[5, 6] == pytest.approx(s / abs(s), abs=1e-14)
+    # Hermitian
+    assert z[3, 2] == pytest.approx(np.conj(z[5, 6]), abs=1e-15)
+
+
+@pytest.mark.parametrize("weight", [O.W_BISPEC, O.W_UNIT])
+def test_recursion_exact_for_single_noise_free_frame(weight):
+    """One frame: B carries the exact phases, so the recursion returns them with zero shift."""
+    N, R = 32, 4
+    rng = np.random.default_rng(11)
+    frames = rng.random((1, N, N)) + 0.5
+    In, _, _ = O.frame_spectra(frames, (0, 0, N, N), N, 3)
+    P, M = O.power_mean(In)
+    pairs = O.pair_domain(N, FC, R)
+    B = O.bispectrum(In, pairs)
+    z = O.phase_recursion(B, pairs, M, N, FC, R, weight)
+    U = O.domain_U(N, FC)
+    c = N // 2
+    got = z[U[:, 1] + c, U[:, 0] + c]
+    exp = In[0][U[:, 1] + c, U[:, 0] + c]
+    exp = exp / np.abs(exp)
+    assert np.max(np.abs(got - exp)) < 1e-10
+
+
+def test_full_path_recovers_diffraction_limited_object():
+    """Seeing-free, noise-free single frame, no window, flat STF.
+
+    Then A = |I_n| T0 and z = I_n / |I_n|, so the sub-image is the frame's
+    spectrum times T0 on the disk, transformed back (checked with numpy.fft).
+    """
+    N, R = 32, 4
+    obj, psfs, frames = _circular_frames(N, 1, 12, psf="diffraction")
+    r = O.reconstruct_subfield(frames, (0, 0, N, N), N, FC, R, 0, np.ones((N, N)))
+    T0 = O.otf_t0(N, FC)
+    spec = np.fft.fftshift(np.fft.fft2(frames[0])) * T0
+    spec[N // 2, N // 2] = 0.0
+    exp = np.real(np.fft.ifft2(np.fft.ifftshift(spec))) + frames[0].mean()
+    assert np.linalg.norm(r["rec"] - exp) / np.linalg.norm(exp) < 1e-10
+
+
+# --------------------------------------------------------------------------- mosaic
+def test_mosaic_undoes_the_window():
+    W, H, N, taper = 150, 110, 64, 8
+    subs = O.subfield_grid(W, H, N, 32)
+    c = 7.25
+    recs = []
+    for (_, _, w, h) in subs:
+        r = np.zeros((N, N))
+        r[:h, :w] = c * O.window2d(w, h, taper)
+        recs.append(r)
+    out, valid = O.mosaic(recs, subs, W, H, taper)
+    assert valid.mean() > 0.8
+    assert np.max(np.abs(out[valid] - c)) < 1e-12
+    assert np.all(out[~valid] == 0)
+    # a pixel covered by exactly one tile near the corner with tiny weight is invalid
+    assert not valid[0, 0]
