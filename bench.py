@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 speckle-masking path on TiO-shaped bursts.
+
+One step = one whole burst through every stage (spectra, power/mean/noise,
+modulus, bispectrum, phase recursion, inverse transform, mosaic) on a
+synthetic 2560x2160x100 uint16 burst already resident in HBM.  ``value`` is
+bursts/s over all ranks; ``e2e`` is the same metric through the serving API
+(sm_submit_burst / sm_poll) from pinned host buffers, host<->device copies
+inside the timed region.  Every input (1.1 GB of frames, 3.5 GB of spectra,
+34 GB of bispectrum) is larger than the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank reconstructs its own bursts (replicas; the
+path has no exchange step), a barrier brackets the timed region and the
+slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (synth config, N, R)
+    "tio2560": ("tio2560", 256, 24),
+    "halpha1024": ("halpha1024", 128, 16),
+    "subfield64": ("subfield64", 64, 8),
+}
+FP32_LANES_PER_SM = 128
+FLOPS_PER_TRIPLE = 14          # two complex products + one complex add
+METRIC = "bursts/sec and p99 latency, served vs plain, 2560x2160x100 at 1e-3 rel L2"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tio2560", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def oracle_sample(workload: str, frames_small=(4, 8)) -> dict:
+    """Time the FP64 oracle, single-threaded, on one subfield at two frame counts,
+    and extrapolate linearly to a whole burst (F frames, every subfield)."""
+    cfg, N, R = WORKLOADS[workload]
+    code = f"""
+import json, os, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from synth import CONFIGS, make_burst
+from oracle import speckle_oracle as O
+spec = CONFIGS[{cfg!r}]
+b = make_burst(spec, F={max(frames_small)}, burst=99)
+subs = O.subfield_grid(spec.W, spec.H, {N}, {N} // 2)
+s = len(subs) // 2
+stf = O.stf_model({N}, 0.2885, b['d_over_r0'])
+t = []
+for F in {tuple(frames_small)!r}:
+    t0 = time.perf_counter()
+    O.reconstruct_subfield(b['frames'][:F], subs[s], {N}, 0.2885, {R}, {N} // 8, stf)
+    t.append(time.perf_counter() - t0)
+print(json.dumps({{"t": t, "n_sub": len(subs), "F": spec.F}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    (f1, f2), (t1, t2) = frames_small, d["t"]
+    per_frame = max((t2 - t1) / (f2 - f1), 0.0)
+    fixed = max(t1 - f1 * per_frame, 0.0)
+    per_burst = d["n_sub"] * (fixed + d["F"] * per_frame)
+    return {"value": 1.0 / per_burst, "unit": "bursts/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle, 1 thread: one {N}x{N} subfield at F={f1} and F={f2} "
+                       f"({t1:.2f} s, {t2:.2f} s), extrapolated linearly in F to {d['F']} frames "
+                       f"x {d['n_sub']} subfields = {per_burst:.0f} s per burst"),
+            "seconds": t1 + t2}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg, N, _ = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, (2, 4))
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        s = oracle_sample(args.workload, (2, 4))
+        vals.append(s["value"])
+        secs += s["seconds"]
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "bursts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{args.workload} burst (FP64 oracle sample)"},
+            "cpu_baseline": {"value": v, "unit": "bursts/s", "cores": 1, "kind": "oracle",
+                             "sample": s["sample"]},
+            "e2e": {"value": v, "unit": "bursts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1701_00581_gb300 import Channel, Engine, Plan, build
+    build.build()
+    from synth import CONFIGS, make_burst
+
+    cfg, N, R = WORKLOADS[args.workload]
+    spec = CONFIGS[cfg]
+    b = make_burst(spec, channel=1, burst=rank, device=f"cuda:{local}")
+    F = spec.F
+    ch = Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=F)
+    plan = Plan(ch, device=local)
+    info = plan.info
+    n_sub = info["n_sub"]
+    stf_np = plan.model_stf(b["d_over_r0"])
+    dev = torch.device("cuda", local)
+    frames = torch.from_numpy(b["frames"]).to(dev)
+    stf = torch.from_numpy(stf_np).to(dev)
+    ws, lay = plan.workspace(F, n_sub)
+    out = torch.empty((spec.H, spec.W), dtype=torch.float32, device=dev)
+    valid = torch.empty((spec.H, spec.W), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        plan.stage_spectra(frames, F, 0, n_sub, ws, lay, stream)
+        plan.stage_stats(F, n_sub, ws, lay, stream)
+        plan.stage_amplitude(n_sub, stf, ws, lay, stream)
+        if ev is not None:
+            ev[0].record(stream)
+        plan.stage_bispectrum(F, n_sub, ws, lay, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        plan.stage_phase(n_sub, ws, lay, stream)
+        plan.stage_inverse(F, 0, n_sub, ws, lay, stream)
+        plan.stage_mosaic(ws, lay, out, valid, stream)
+
+    launches_per_step = 7
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(args.steps):
+        step(bev[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+    bisp_ms = statistics.mean(a.elapsed_time(c) for a, c in bev)
+    tmax = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = world * args.steps / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel (bispectrum): FP32 ALU bound
+    triples = info["n_pairs"] * F * n_sub
+    achieved = FLOPS_PER_TRIPLE * triples / (bisp_ms / 1000.0) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_max = 2070.0
+    if os.path.exists(peaks_path):
+        sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max))
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_bispectrum", "kernel_ms": round(bisp_ms, 3),
+                "note": (f"{FLOPS_PER_TRIPLE} flops x {triples:.3e} used triples per launch; peak = "
+                         f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                         f"{sm_max:.0f} MHz")}
+
+    # end to end through the serving API, host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        del ws
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        host_frames = torch.from_numpy(b["frames"]).pin_memory()
+        host_out = [torch.empty((spec.H, spec.W), dtype=torch.float32).pin_memory() for _ in range(2)]
+        host_valid = [torch.empty((spec.H, spec.W), dtype=torch.uint8).pin_memory() for _ in range(2)]
+        eng = Engine([ch], hbm_budget_bytes=int(100e9), max_inflight=2, device=local)
+        fr_np = host_frames.numpy()
+        d_r0 = b["d_over_r0"]
+
+        def serve(n):
+            pending, lat = [], []
+            submitted = done = 0
+            t_start = time.perf_counter()
+            while done < n:
+                while submitted < n and len(pending) < 2:
+                    k = submitted % 2
+                    tk = eng.try_submit(0, fr_np, host_out[k].numpy(), host_valid[k].numpy(),
+                                        d_over_r0=d_r0)
+                    if tk is None:
+                        break
+                    pending.append((tk, time.perf_counter()))
+                    submitted += 1
+                tk, ts = pending.pop(0)
+                eng.poll(tk, -1)
+                lat.append(time.perf_counter() - ts)
+                done += 1
+            return time.perf_counter() - t_start, lat
+
+        serve(max(1, args.warmup))
+        if world > 1:
+            dist.barrier()
+        el, lat = serve(args.steps)
+        tt = torch.tensor([el], device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        eng.close()
+        e2e = {"value": world * args.steps / float(tt.item()), "unit": "bursts/s",
+               "h2d_bytes_per_step": int(b["frames"].nbytes + N * N * 8),
+               "d2h_bytes_per_step": int(spec.W * spec.H * 5),
+               "latency_ms_p50": 1000 * float(np.percentile(lat, 50)),
+               "latency_ms_p99": 1000 * float(np.percentile(lat, 99)),
+               "max_inflight": 2}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu = oracle_sample(args.workload)
+            cpu.pop("seconds", None)
+        except Exception as e:  # reported, never fatal
+            cpu = {"value": None, "error": str(e)[-300:]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "bursts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{args.workload} burst: {spec.W}x{spec.H}x{F} uint16, "
+                                       f"{n_sub} subfields of {N}^2 at 50% overlap, |v|<={R}",
+                           "path": "plain per-burst stages, FP32 spectra, FP64 phase",
+                           "l2": "inputs larger than L2 (no flush)",
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": launches_per_step * args.steps,
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

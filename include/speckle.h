@@ -1,0 +1,243 @@
+/*
+ * speckle.h -- C ABI of the GB300 speckle-masking reconstruction library.
+ *
+ * The library reconstructs one diffraction-limited image from a burst of F
+ * short-exposure frames by speckle masking, subfield by subfield, as the
+ * paper describes it (Li et al., "High Performance Parallel Image
+ * Reconstruction for New Vacuum Solar Telescope"):
+ *
+ *   Sect. 2      frames are cut into partially overlapping subfields (the
+ *                isoplanatic patch) that are processed independently;
+ *   Sect. 2, 3.2 every subfield frame is Fourier transformed; the object's
+ *                Fourier modulus comes from the mean power spectrum over
+ *                the speckle transfer function (Eq. 1); its Fourier phase
+ *                comes from the mean bispectrum by speckle masking;
+ *   Sect. 2, 3.2 modulus and phase are transformed back and the overlapping
+ *                sub-images are merged into one mosaic.
+ *
+ * Every step runs in hand-written CUDA kernels for sm_103a.  All entry
+ * points return an int status (SM_OK = 0, SM_PENDING = 1, negative =
+ * error); none throws or aborts.  Device pointers are plain CUDA device
+ * addresses on the plan's / engine's device; a "stream" argument is a
+ * cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Frequency conventions used by every layout below:
+ *   k = (kx, ky) in DFT bins of the N-point transform, centred in
+ *   [-N/2, N/2); r = fc * N is the optics cutoff radius; K = floor(r);
+ *   U = {|k| <= r}; H = upper half plane {ky > 0 or (ky == 0 and kx > 0)};
+ *   V = {0 < |v| <= R}.
+ */
+#ifndef SPECKLE_GB300_H
+#define SPECKLE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SM_OK         0
+#define SM_PENDING    1   /* sm_poll: ticket not finished yet                */
+#define SM_EINVAL    -1   /* bad argument or configuration                    */
+#define SM_ENOMEM    -2   /* request larger than the memory budget            */
+#define SM_EBUSY     -3   /* no free slot now; retry after a poll             */
+#define SM_ETIMEDOUT -4   /* sm_poll timeout elapsed                          */
+#define SM_ECUDA     -5   /* a CUDA call failed (message: sm_last_error)      */
+#define SM_ECANCELED -6   /* ticket cancelled by sm_close                     */
+#define SM_ENOTFOUND -7   /* unknown ticket                                   */
+
+/* ---- enums ------------------------------------------------------------- */
+#define SM_FP32 0         /* frame spectra stored as float2                   */
+#define SM_FP16 1         /* frame spectra stored as half2 (scaled by 2^14)   */
+#define SM_BF16 2         /* frame spectra stored as bfloat162                */
+
+#define SM_W_BISPEC 0     /* phase terms weighted by |B| (plain phasor sum)   */
+#define SM_W_UNIT   1     /* unit-modulus phase terms                         */
+
+#define SM_U16 0          /* frame samples: uint16 counts                     */
+#define SM_F32 1          /* frame samples: float32                           */
+
+/* ---- one camera channel ------------------------------------------------ */
+typedef struct {
+    int    W, H;          /* frame size in px (Table 1: 2560x2160, 1024x1024)  */
+    int    N;             /* subfield size = DFT size: 64, 128 or 256          */
+    int    stride;        /* subfield step in px (N/2 = 50 % overlap)          */
+    int    R;             /* bispectrum offset radius, DFT bins, 1 <= R <= K   */
+    double fc;            /* optics cutoff in cycles/px (0 < fc < 0.5)         */
+    int    taper;         /* apodisation ramp width in px (0 = none, <= N/4)   */
+    int    spectra_prec;  /* SM_FP32 / SM_FP16 / SM_BF16                       */
+    int    phase_weight;  /* SM_W_BISPEC / SM_W_UNIT                           */
+    double ck;            /* Korff constant of the model STF (e.g. 0.435)      */
+    int    max_frames;    /* largest burst length F accepted (>= 1)            */
+} sm_channel;
+
+/* ======================================================================== *
+ *  Plan: everything that depends only on the channel (subfield grid, pair  *
+ *  tiles, recursion schedule, twiddles, windows), built once on the host   *
+ *  and uploaded to the device.                                             *
+ * ======================================================================== */
+typedef struct sm_plan sm_plan;
+
+typedef struct {
+    int    n_sub;          /* subfields per frame (Sect. 2 division)           */
+    int    nsx, nsy;       /* subfield grid, row-major: s = j * nsx + i        */
+    int    N, K, R;        /* DFT size, floor(fc*N), offset radius             */
+    int    box_rows;       /* spectrum box rows: ky = -R .. K                  */
+    int    box_cols;       /* 2K+1 columns: kx = -K .. K                       */
+    int    box_pitch;      /* row pitch of every box, elements                 */
+    int    hb_rows;        /* half box rows: ky = 0 .. K (pitch box_pitch)     */
+    int    n_tiles;        /* bispectrum tiles per subfield                    */
+    int    tile_pairs;     /* (w, v) slots per tile                            */
+    long long n_pairs;     /* used (w, v) pairs per subfield                   */
+    int    n_rings;        /* recursion rings (|w|^2 >= 2)                     */
+    int    n_points;       /* recursion points in H with |w|^2 >= 2            */
+    int    n_U;            /* |U|                                              */
+    int    n_V;            /* |V|                                              */
+} sm_plan_info;
+
+/* Build a plan on `device`.  Validates every field of *ch (SM_EINVAL). */
+int sm_plan_create(const sm_channel* ch, int device, sm_plan** out);
+int sm_plan_destroy(sm_plan* plan);
+int sm_plan_get_info(const sm_plan* plan, sm_plan_info* info);
+/* Subfield rectangles (x0, y0, w, h) in host memory, [n_sub][4] ints. */
+int sm_plan_subfields(const sm_plan* plan, int* xywh);
+
+/* Position of the bispectrum value B(w - v, v) of pair (w, v) in the per-
+ * subfield B buffer (units of complex values), for n host pairs given as
+ * int[4] = (wx, wy, vx, vy); -1 where the pair is not stored.  Host only. */
+int sm_plan_pair_index(const sm_plan* plan, long long n, const int* wv, long long* idx);
+
+/* ======================================================================== *
+ *  Workspace: one device allocation holding the per-chunk buffers of the   *
+ *  stage entry points.  The caller allocates ws_bytes (256-B aligned) and  *
+ *  owns it; the library never allocates on these paths.                    *
+ * ======================================================================== */
+typedef struct {
+    /* byte offsets into the workspace of each buffer, for `nsub_chunk`
+     * subfields of F frames (layouts documented per field)                  */
+    size_t spec;   /* [nsub][F][box_rows][box_pitch] complex (prec-sized)    */
+    size_t flux;   /* [nsub][F] float: windowed flux of each frame tile       */
+    size_t mu;     /* [nsub][F] float: windowed mean of each frame tile       */
+    size_t P;      /* [nsub][hb_rows][box_pitch] float: mean power (Eq. 1)    */
+    size_t M;      /* [nsub][hb_rows][box_pitch] float2: mean spectrum        */
+    size_t noise;  /* [nsub] float: additive-noise floor of P                 */
+    size_t A;      /* [nsub][hb_rows][box_pitch] float: object modulus        */
+    size_t B;      /* [nsub][n_tiles][tile_pairs] float2: mean bispectrum     */
+    size_t z;      /* [nsub][hb_rows][box_pitch] double2: unit phasors        */
+    size_t rec;    /* [n_sub total][N][N] float: sub-images of all subfields  */
+    size_t bytes;  /* total workspace size                                    */
+} sm_workspace_layout;
+
+/* Workspace layout for chunks of `nsub_chunk` subfields of F frames. */
+int sm_workspace_query(const sm_plan* plan, int F, int nsub_chunk, sm_workspace_layout* lay);
+
+/* ---- stage entry points (device pointers, asynchronous on `stream`) ----
+ * `sub0` is the first subfield of the chunk (0 .. n_sub-1), `nsub` its
+ * length (<= nsub_chunk of the layout); per-chunk buffers start at the
+ * chunk's first subfield, `rec` is indexed by absolute subfield.           */
+
+/* Sect. 2: cut, apodise, mean-subtract, 2-D DFT and normalise every frame
+ * tile of subfields sub0..sub0+nsub-1.  frames: device [F][H][W] samples of
+ * `frame_type`.  Writes spec, flux, mu.                                     */
+int sm_stage_spectra(const sm_plan* plan, const void* frames, int frame_type, int F,
+                     int sub0, int nsub, void* ws, const sm_workspace_layout* lay,
+                     void* stream);
+
+/* Eq. 1 numerator: P = <|I_i|^2>, M = <I_i> over the frames on the half box;
+ * noise = mean P over the half-box corners outside the cutoff.             */
+int sm_stage_stats(const sm_plan* plan, int F, int nsub, void* ws,
+                   const sm_workspace_layout* lay, void* stream);
+
+/* Eq. 1: A = sqrt(max(P - noise, 0) / max(STF, 1e-4)) * T0 on U.  stf is a
+ * device double [N][N] table, centred (index (ky+N/2)*N + kx+N/2).        */
+int sm_stage_amplitude(const sm_plan* plan, int nsub, const double* stf, void* ws,
+                       const sm_workspace_layout* lay, void* stream);
+
+/* Sect. 2, 3.2 (speckle masking): mean bispectrum
+ * B(w-v, v) = (1/F) sum_i I_i(w-v) I_i(v) conj I_i(w) on every pair the
+ * phase recursion reads.                                                    */
+int sm_stage_bispectrum(const sm_plan* plan, int F, int nsub, void* ws,
+                        const sm_workspace_layout* lay, void* stream);
+
+/* Sect. 3.2 (LWW recursion): unit phasors z on the half box, ring by ring
+ * from the anchors z(e_x), z(e_y) = M/|M|.                                  */
+int sm_stage_phase(const sm_plan* plan, int nsub, void* ws,
+                   const sm_workspace_layout* lay, void* stream);
+
+/* Sect. 2: sub-image rec = Re IDFT(A z) * <flux> + <mu> * window, for
+ * subfields sub0..sub0+nsub-1, into rec[sub].                              */
+int sm_stage_inverse(const sm_plan* plan, int F, int sub0, int nsub, void* ws,
+                     const sm_workspace_layout* lay, void* stream);
+
+/* Sect. 3.2 merge: out = sum_s rec_s / sum_s window_s over all subfields;
+ * valid = (sum window >= 0.25), out = 0 elsewhere.  out: device float
+ * [H][W]; valid: device uint8 [H][W] or NULL.                               */
+int sm_stage_mosaic(const sm_plan* plan, void* ws, const sm_workspace_layout* lay,
+                    float* out, uint8_t* valid, void* stream);
+
+/* Whole path on device data: chunks of lay->... subfields through every
+ * stage, then the mosaic.  Asynchronous on `stream`.                       */
+int sm_reconstruct(const sm_plan* plan, const void* frames, int frame_type, int F,
+                   const double* stf, int nsub_chunk, void* ws,
+                   const sm_workspace_layout* lay, float* out, uint8_t* valid, void* stream);
+
+/* Model STF (Sect. 3.2, calibrated by r0): per frame
+ * T0^2 exp(-6.88 (rho D/r0)^(5/3)) + ck (r0/D)^2 T0, averaged over the F
+ * frames' D/r0 and normalised to 1 at k = 0.  Host only; stf_out is host
+ * double [N][N], centred.                                                   */
+int sm_model_stf(const sm_channel* ch, int F, const double* d_over_r0, double* stf_out);
+
+/* ======================================================================== *
+ *  Serving engine: bursts from several channels admitted as device slots   *
+ *  free up, processed concurrently, results polled by ticket.              *
+ * ======================================================================== */
+typedef struct sm_handle sm_handle;
+
+typedef struct {
+    int               n_channels;
+    const sm_channel* ch;               /* [n_channels]                         */
+    size_t            hbm_budget_bytes; /* device memory the engine may hold     */
+    int               max_inflight;     /* bursts on the device at once (>= 1)   */
+    int               device;
+} sm_config;
+
+typedef struct {
+    int            channel;
+    int            F;                   /* frames in this burst (<= max_frames)  */
+    const void*    frames;              /* [F][H][W] of frame_type               */
+    int            frame_type;          /* SM_U16 / SM_F32                        */
+    int            frames_on_device;    /* 1: frames is a device pointer          */
+    const double*  stf;                 /* host [N][N] centred, or NULL           */
+    const double*  d_over_r0;           /* host [F]; used when stf == NULL        */
+    float*         out;                 /* host [H][W], caller-owned              */
+    uint8_t*       valid;               /* host [H][W] or NULL                    */
+} sm_burst;
+
+typedef struct {
+    int    status;                      /* SM_OK, SM_PENDING or an error          */
+    double t_submit_ms;                 /* engine clock at submit return          */
+    double t_done_ms;                   /* engine clock when the result was ready */
+    double gpu_ms;                      /* device time of the burst's work        */
+    size_t bytes_admitted;              /* device bytes held by the burst         */
+} sm_result;
+
+int sm_open(const sm_config* cfg, sm_handle** out);
+/* Stage one burst: copies the frames to the device (the caller may reuse
+ * them on return) and queues its work.  SM_EBUSY when no slot is free.     */
+int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket);
+/* Wait up to timeout_ms (0 = test, <0 = forever).  SM_OK once the mosaic
+ * has been copied into b->out; then the ticket is released.               */
+int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result* res);
+/* Cancel pending tickets, wait for the device, free everything.           */
+int sm_close(sm_handle* h);
+
+const char* sm_strerror(int status);
+/* Last CUDA or validation message of this thread (never NULL). */
+const char* sm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPECKLE_GB300_H */

@@ -1,0 +1,240 @@
+"""GB300 speckle-masking reconstruction (Li et al., arXiv:1701.00581), Python side.
+
+A thin binding of the C ABI in ``include/speckle.h``: it marshals arguments,
+and uses PyTorch only for device memory and streams.  Every step of the
+reconstruction runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import (SM_BF16, SM_F32, SM_FP16, SM_FP32, SM_U16, SM_W_BISPEC,  # noqa: F401
+                   SM_W_UNIT, SpeckleError, check, load)
+
+__all__ = ["Channel", "Plan", "Engine", "load", "SpeckleError"]
+
+
+@dataclasses.dataclass
+class Channel:
+    """One camera channel (sm_channel)."""
+    W: int
+    H: int
+    N: int
+    R: int
+    stride: Optional[int] = None
+    fc: float = 0.2885
+    taper: Optional[int] = None
+    spectra_prec: int = SM_FP32
+    phase_weight: int = SM_W_BISPEC
+    ck: float = 0.435
+    max_frames: int = 100
+
+    def to_c(self) -> _lib.sm_channel:
+        return _lib.sm_channel(
+            self.W, self.H, self.N, self.stride if self.stride is not None else self.N // 2, self.R,
+            self.fc, self.taper if self.taper is not None else self.N // 8, self.spectra_prec,
+            self.phase_weight, self.ck, self.max_frames)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """sm_plan: tables of one channel on one device, plus the stage calls."""
+
+    def __init__(self, ch: Channel, device: int = 0):
+        self.lib = load()
+        self.ch = ch
+        self.device = device
+        self._c = ch.to_c()
+        h = C.c_void_p()
+        check(self.lib.sm_plan_create(C.byref(self._c), device, C.byref(h)), "sm_plan_create")
+        self.h = h
+        inf = _lib.sm_plan_info()
+        check(self.lib.sm_plan_get_info(self.h, C.byref(inf)), "sm_plan_get_info")
+        self.info = {n: getattr(inf, n) for n, _ in _lib.sm_plan_info._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.sm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- host queries -------------------------------------------------------
+    def subfields(self) -> np.ndarray:
+        out = np.zeros((self.info["n_sub"], 4), dtype=np.int32)
+        check(self.lib.sm_plan_subfields(self.h, out.ctypes.data), "sm_plan_subfields")
+        return out
+
+    def pair_index(self, wv: np.ndarray) -> np.ndarray:
+        wv = np.ascontiguousarray(wv, dtype=np.int32).reshape(-1, 4)
+        idx = np.zeros(len(wv), dtype=np.int64)
+        check(self.lib.sm_plan_pair_index(self.h, len(wv), wv.ctypes.data, idx.ctypes.data),
+              "sm_plan_pair_index")
+        return idx
+
+    def model_stf(self, d_over_r0: Sequence[float]) -> np.ndarray:
+        d = np.ascontiguousarray(d_over_r0, dtype=np.float64)
+        out = np.zeros((self.ch.N, self.ch.N))
+        check(self.lib.sm_model_stf(C.byref(self._c), len(d), d.ctypes.data, out.ctypes.data),
+              "sm_model_stf")
+        return out
+
+    def layout(self, F: int, chunk: int) -> _lib.sm_workspace_layout:
+        lay = _lib.sm_workspace_layout()
+        check(self.lib.sm_workspace_query(self.h, F, chunk, C.byref(lay)), "sm_workspace_query")
+        return lay
+
+    # ---- device buffers -----------------------------------------------------
+    def workspace(self, F: int, chunk: int):
+        import torch
+        lay = self.layout(F, chunk)
+        ws = torch.empty(lay.bytes + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
+        off = (-ws.data_ptr()) % 256
+        return ws[off:off + lay.bytes], lay
+
+    def views(self, ws, lay, F: int, nsub: int) -> Dict[str, "torch.Tensor"]:
+        """Typed tensor views of the workspace buffers (layouts of speckle.h)."""
+        import torch
+        i = self.info
+        box = i["box_rows"] * i["box_pitch"]
+        hb = i["hb_rows"] * i["box_pitch"]
+
+        def v(off, n, dt, shape):
+            nb = n * torch.empty((), dtype=dt).element_size()
+            return ws[off:off + nb].view(dt).reshape(shape)
+
+        prec = self.ch.spectra_prec
+        if prec == SM_FP32:
+            spec = v(lay.spec, nsub * F * box, torch.complex64, (nsub, F, i["box_rows"], i["box_pitch"]))
+        else:
+            dt = torch.float16 if prec == SM_FP16 else torch.bfloat16
+            spec = v(lay.spec, nsub * F * box * 2, dt, (nsub, F, i["box_rows"], i["box_pitch"], 2))
+        N = i["N"]
+        return {
+            "spec": spec,
+            "flux": v(lay.flux, nsub * F, torch.float32, (nsub, F)),
+            "mu": v(lay.mu, nsub * F, torch.float32, (nsub, F)),
+            "P": v(lay.P, nsub * hb, torch.float32, (nsub, i["hb_rows"], i["box_pitch"])),
+            "M": v(lay.M, nsub * hb, torch.complex64, (nsub, i["hb_rows"], i["box_pitch"])),
+            "noise": v(lay.noise, nsub, torch.float32, (nsub,)),
+            "A": v(lay.A, nsub * hb, torch.float32, (nsub, i["hb_rows"], i["box_pitch"])),
+            "B": v(lay.B, nsub * i["n_tiles"] * i["tile_pairs"], torch.complex64,
+                   (nsub, i["n_tiles"] * i["tile_pairs"])),
+            "z": v(lay.z, nsub * hb, torch.complex128, (nsub, i["hb_rows"], i["box_pitch"])),
+            "rec": v(lay.rec, i["n_sub"] * N * N, torch.float32, (i["n_sub"], N, N)),
+        }
+
+    # ---- stage entry points (device tensors) -------------------------------
+    def stage_spectra(self, frames, F, sub0, nsub, ws, lay, stream=None):
+        ft = SM_U16 if frames.dtype.__str__().endswith("uint16") else SM_F32
+        check(self.lib.sm_stage_spectra(self.h, _ptr(frames), ft, F, sub0, nsub, _ptr(ws), C.byref(lay),
+                                        _stream(stream)), "sm_stage_spectra")
+
+    def stage_stats(self, F, nsub, ws, lay, stream=None):
+        check(self.lib.sm_stage_stats(self.h, F, nsub, _ptr(ws), C.byref(lay), _stream(stream)),
+              "sm_stage_stats")
+
+    def stage_amplitude(self, nsub, stf, ws, lay, stream=None):
+        check(self.lib.sm_stage_amplitude(self.h, nsub, _ptr(stf), _ptr(ws), C.byref(lay), _stream(stream)),
+              "sm_stage_amplitude")
+
+    def stage_bispectrum(self, F, nsub, ws, lay, stream=None):
+        check(self.lib.sm_stage_bispectrum(self.h, F, nsub, _ptr(ws), C.byref(lay), _stream(stream)),
+              "sm_stage_bispectrum")
+
+    def stage_phase(self, nsub, ws, lay, stream=None):
+        check(self.lib.sm_stage_phase(self.h, nsub, _ptr(ws), C.byref(lay), _stream(stream)), "sm_stage_phase")
+
+    def stage_inverse(self, F, sub0, nsub, ws, lay, stream=None):
+        check(self.lib.sm_stage_inverse(self.h, F, sub0, nsub, _ptr(ws), C.byref(lay), _stream(stream)),
+              "sm_stage_inverse")
+
+    def stage_mosaic(self, ws, lay, out, valid=None, stream=None):
+        check(self.lib.sm_stage_mosaic(self.h, _ptr(ws), C.byref(lay), _ptr(out), _ptr(valid),
+                                       _stream(stream)), "sm_stage_mosaic")
+
+    def reconstruct(self, frames, F, stf, chunk, ws, lay, out, valid=None, stream=None):
+        ft = SM_U16 if str(frames.dtype).endswith("uint16") else SM_F32
+        check(self.lib.sm_reconstruct(self.h, _ptr(frames), ft, F, _ptr(stf), chunk, _ptr(ws), C.byref(lay),
+                                      _ptr(out), _ptr(valid), _stream(stream)), "sm_reconstruct")
+
+
+class Engine:
+    """sm_open / sm_submit_burst / sm_poll / sm_close (the serving engine)."""
+
+    def __init__(self, channels: Sequence[Channel], hbm_budget_bytes: int, max_inflight: int = 2,
+                 device: int = 0):
+        self.lib = load()
+        self._ch = (_lib.sm_channel * len(channels))(*[c.to_c() for c in channels])
+        self.channels = list(channels)
+        cfg = _lib.sm_config(len(channels), self._ch, hbm_budget_bytes, max_inflight, device)
+        h = C.c_void_p()
+        check(self.lib.sm_open(C.byref(cfg), C.byref(h)), "sm_open")
+        self.h = h
+        self._keep: Dict[int, tuple] = {}
+
+    def submit(self, channel: int, frames, out: np.ndarray, valid: Optional[np.ndarray] = None,
+               stf: Optional[np.ndarray] = None, d_over_r0: Optional[np.ndarray] = None) -> int:
+        """Returns a ticket, or raises SpeckleError (status SM_EBUSY when no slot is free)."""
+        on_dev = not isinstance(frames, np.ndarray)
+        ft = SM_U16 if str(frames.dtype).endswith("uint16") else SM_F32
+        stf = None if stf is None else np.ascontiguousarray(stf, dtype=np.float64)
+        d = None if d_over_r0 is None else np.ascontiguousarray(d_over_r0, dtype=np.float64)
+        b = _lib.sm_burst(channel, frames.shape[0], _ptr(frames), ft, 1 if on_dev else 0,
+                          _ptr(stf), _ptr(d), _ptr(out), _ptr(valid))
+        t = C.c_uint64()
+        check(self.lib.sm_submit_burst(self.h, C.byref(b), C.byref(t)), "sm_submit_burst")
+        self._keep[t.value] = (out, valid)
+        return t.value
+
+    def try_submit(self, *args, **kw) -> Optional[int]:
+        try:
+            return self.submit(*args, **kw)
+        except SpeckleError as e:
+            if e.status == _lib.SM_EBUSY:
+                return None
+            raise
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        res = _lib.sm_result()
+        st = self.lib.sm_poll(self.h, ticket, timeout_ms, C.byref(res))
+        if st in (_lib.SM_PENDING, _lib.SM_ETIMEDOUT):
+            return st, None
+        check(st, "sm_poll")
+        self._keep.pop(ticket, None)
+        return st, {"t_submit_ms": res.t_submit_ms, "t_done_ms": res.t_done_ms, "gpu_ms": res.gpu_ms,
+                    "bytes_admitted": res.bytes_admitted}
+
+    def close(self):
+        if self.h:
+            self.lib.sm_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

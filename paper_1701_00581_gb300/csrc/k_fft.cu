@@ -1,0 +1,338 @@
+// Subfield spectra (Sect. 2: Fourier transform of every subimage) and the
+// inverse transform of modulus and phase (Sect. 2, Sect. 3.2).
+//
+// One CTA per (frame, subfield): the tile is cut from the frame, apodised by
+// the separable window, its windowed mean is subtracted, and the 2-D DFT is
+// taken as real row FFTs (two rows packed per complex FFT) followed by
+// column FFTs of only the K+1 non-negative columns inside the cutoff box.
+// Each FFT is a radix-2 Stockham transform run by one warp in shared memory.
+#include "sm_internal.h"
+
+namespace {
+
+using smi::PlanDev;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Radix-2 Stockham FFT of length N by one warp.  a holds the input, b is
+// scratch; returns the buffer holding the output in natural order.
+// INV = true uses exp(+2 pi i k / N) (unnormalised inverse).
+template <int N, bool INV>
+__device__ __forceinline__ float2* warp_fft(float2* a, float2* b, const float2* tw, int lane) {
+#pragma unroll
+    for (int Ns = 1; Ns < N; Ns <<= 1) {
+#pragma unroll
+        for (int j = lane; j < N / 2; j += 32) {
+            const int k = j & (Ns - 1);
+            float2 w = tw[k * (N / (2 * Ns))];
+            if (INV) w.y = -w.y;
+            const float2 a0 = a[j];
+            const float2 t = cmul(a[j + N / 2], w);
+            const int o = 2 * j - k;
+            b[o] = make_float2(a0.x + t.x, a0.y + t.y);
+            b[o + Ns] = make_float2(a0.x - t.x, a0.y - t.y);
+        }
+        __syncwarp();
+        float2* t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+__device__ __forceinline__ float load_sample(const uint16_t* p) { return (float)__ldg(p); }
+__device__ __forceinline__ float load_sample(const float* p) { return __ldg(p); }
+
+template <int PREC>
+__device__ __forceinline__ void store_spec(void* spec, size_t idx, float2 v) {
+    if (PREC == SM_FP32) {
+        reinterpret_cast<float2*>(spec)[idx] = v;
+    } else if (PREC == SM_FP16) {
+        reinterpret_cast<__half2*>(spec)[idx] =
+            __floats2half2_rn(v.x * smi::FP16_SCALE, v.y * smi::FP16_SCALE);
+    } else {
+        reinterpret_cast<__nv_bfloat162*>(spec)[idx] = __floats2bfloat162_rn(v.x, v.y);
+    }
+}
+
+constexpr int FFT_THREADS = 256;
+constexpr int FFT_WARPS = FFT_THREADS / 32;
+
+__host__ __device__ constexpr size_t fft_smem(int N, int K) {
+    return (size_t)(K + 1) * (N + 1) * sizeof(float2)        // column buffer
+           + (size_t)FFT_WARPS * 2 * N * sizeof(float2)      // per-warp ping-pong
+           + (size_t)N * sizeof(float2)                      // twiddles
+           + (size_t)2 * N * sizeof(float)                   // windows
+           + (size_t)FFT_WARPS * 2 * sizeof(double);         // reductions
+}
+
+template <int N, typename TIn, int PREC>
+__global__ void __launch_bounds__(FFT_THREADS, 1)
+k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __restrict__ spec,
+          float* __restrict__ flux, float* __restrict__ mu) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K1 = p.K + 1, CP = N + 1;
+    float2* C = reinterpret_cast<float2*>(smem);
+    float2* scratch = C + (size_t)K1 * CP;
+    float2* stw = scratch + FFT_WARPS * 2 * N;
+    float* swx = reinterpret_cast<float*>(stw + N);
+    float* swy = swx + N;
+    double* red = reinterpret_cast<double*>(swy + N);
+
+    const int f = blockIdx.x, sl = blockIdx.y, s = sub0 + sl;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int4 sb = p.subs[s];
+    const int x0 = sb.x, y0 = sb.y, w = sb.z, h = sb.w;
+    for (int i = tid; i < N; i += FFT_THREADS) {
+        stw[i] = p.tw[i];
+        swx[i] = p.winx[(size_t)s * N + i];
+        swy[i] = p.winy[(size_t)s * N + i];
+    }
+    __syncthreads();
+
+    const TIn* fr = frames + (size_t)f * p.H * p.W;
+    // pass 1: windowed mean of the tile
+    float acc = 0.f;
+    for (int e = tid; e < w * h; e += FFT_THREADS) {
+        const int y = e / w, x = e - y * w;
+        acc += swx[x] * swy[y] * load_sample(fr + (size_t)(y0 + y) * p.W + x0 + x);
+    }
+    double dacc = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if (lane == 0) red[warp] = dacc;
+    __syncthreads();
+    double tot = 0.0;
+    for (int i = 0; i < FFT_WARPS; ++i) tot += red[i];
+    const double wsum = p.winsum[s];
+    const float mean = (float)(tot / wsum);
+
+    // pass 2: row FFTs, two real rows per complex FFT, keep kx = 0..K
+    float2* fa = scratch + warp * 2 * N;
+    float2* fb = fa + N;
+    for (int pr = warp; pr < N / 2; pr += FFT_WARPS) {
+        const int y1 = 2 * pr, y2 = y1 + 1;
+        if (y1 >= h) {
+            for (int kx = lane; kx < K1; kx += 32) {
+                C[kx * CP + y1] = make_float2(0.f, 0.f);
+                C[kx * CP + y2] = make_float2(0.f, 0.f);
+            }
+            continue;
+        }
+        const bool has2 = y2 < h;
+        const TIn* r1 = fr + (size_t)(y0 + y1) * p.W + x0;
+        const TIn* r2 = fr + (size_t)(y0 + (has2 ? y2 : y1)) * p.W + x0;
+        for (int x = lane; x < N; x += 32) {
+            float v1 = 0.f, v2 = 0.f;
+            if (x < w) {
+                v1 = swx[x] * swy[y1] * (load_sample(r1 + x) - mean);
+                if (has2) v2 = swx[x] * swy[y2] * (load_sample(r2 + x) - mean);
+            }
+            fa[x] = make_float2(v1, v2);
+        }
+        __syncwarp();
+        const float2* Z = warp_fft<N, false>(fa, fb, stw, lane);
+        for (int kx = lane; kx < K1; kx += 32) {
+            const float2 za = Z[kx], zb = Z[(N - kx) & (N - 1)];
+            C[kx * CP + y1] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+            C[kx * CP + y2] = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // pass 3: column FFTs of kx = 0..K
+    for (int kx = warp; kx < K1; kx += FFT_WARPS) {
+        float2* col = C + (size_t)kx * CP;
+        for (int y = lane; y < N; y += 32) fa[y] = col[y];
+        __syncwarp();
+        const float2* Z = warp_fft<N, false>(fa, fb, stw, lane);
+        for (int y = lane; y < N; y += 32) col[y] = Z[y];
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // pass 4: normalise by the windowed flux and store the box ky = -R..K
+    const double fl = (double)mean * wsum;
+    const float inv = (float)(1.0 / fl);
+    const size_t base = ((size_t)sl * F + f) * p.box_rows * p.box_pitch;
+    const int nbox = p.box_rows * p.box_cols;
+    for (int e = tid; e < nbox; e += FFT_THREADS) {
+        const int row = e / p.box_cols, col = e - row * p.box_cols;
+        const int ky = row - p.R, kx = col - p.K;
+        float2 v;
+        if (kx >= 0) {
+            v = C[kx * CP + (ky & (N - 1))];
+        } else {
+            v = C[(-kx) * CP + ((-ky) & (N - 1))];
+            v.y = -v.y;
+        }
+        v.x *= inv;
+        v.y *= inv;
+        if (kx == 0 && ky == 0) v = make_float2(1.f, 0.f);
+        store_spec<PREC>(spec, base + (size_t)row * p.box_pitch + col, v);
+    }
+    if (tid == 0) {
+        flux[(size_t)sl * F + f] = (float)fl;
+        mu[(size_t)sl * F + f] = mean;
+    }
+}
+
+// Inverse: O = A z on the disk (Hermitian), DC removed; columns first, then
+// pairs of Hermitian rows packed into one complex inverse FFT.
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS, 1)
+k_inverse(PlanDev p, int F, int sub0, const float* __restrict__ A, const double2* __restrict__ z,
+          const float* __restrict__ flux, const float* __restrict__ mu, float* __restrict__ rec) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K = p.K, K1 = K + 1, CP = N + 1;
+    float2* C = reinterpret_cast<float2*>(smem);
+    float2* scratch = C + (size_t)K1 * CP;
+    float2* stw = scratch + FFT_WARPS * 2 * N;
+    float* swx = reinterpret_cast<float*>(stw + N);
+    float* swy = swx + N;
+    double* red = reinterpret_cast<double*>(swy + N);
+
+    const int sl = blockIdx.x, s = sub0 + sl;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < N; i += FFT_THREADS) {
+        stw[i] = p.tw[i];
+        swx[i] = p.winx[(size_t)s * N + i];
+        swy[i] = p.winy[(size_t)s * N + i];
+    }
+    if (tid == 0) {
+        double fs = 0.0, ms = 0.0;
+        for (int f = 0; f < F; ++f) {
+            fs += flux[(size_t)sl * F + f];
+            ms += mu[(size_t)sl * F + f];
+        }
+        red[0] = fs / F;
+        red[1] = ms / F;
+    }
+    const size_t hb = (size_t)p.hb_rows * p.box_pitch;
+    const float* As = A + (size_t)sl * hb;
+    const double2* zs = z + (size_t)sl * hb;
+    for (int e = tid; e < K1 * N; e += FFT_THREADS) {
+        const int kx = e / N, j = e - kx * N;
+        const int ky = j < N / 2 ? j : j - N;
+        float2 v = make_float2(0.f, 0.f);
+        if (kx * kx + ky * ky <= p.r2i && (kx | ky) != 0 && ky >= -K && ky <= K) {
+            if (ky > 0 || (ky == 0 && kx > 0)) {
+                const size_t o = (size_t)ky * p.box_pitch + kx + K;
+                const double2 zz = zs[o];
+                v = make_float2((float)(As[o] * zz.x), (float)(As[o] * zz.y));
+            } else {
+                const size_t o = (size_t)(-ky) * p.box_pitch + (-kx) + K;
+                const double2 zz = zs[o];
+                v = make_float2((float)(As[o] * zz.x), (float)(-As[o] * zz.y));
+            }
+        }
+        C[kx * CP + j] = v;
+    }
+    __syncthreads();
+    const double fmean = red[0];
+    const float mmean = (float)red[1];
+    const float scale = (float)(fmean / ((double)N * N));
+
+    float2* fa = scratch + warp * 2 * N;
+    float2* fb = fa + N;
+    for (int kx = warp; kx < K1; kx += FFT_WARPS) {
+        float2* col = C + (size_t)kx * CP;
+        for (int y = lane; y < N; y += 32) fa[y] = col[y];
+        __syncwarp();
+        const float2* Zc = warp_fft<N, true>(fa, fb, stw, lane);
+        for (int y = lane; y < N; y += 32) col[y] = Zc[y];
+        __syncwarp();
+    }
+    __syncthreads();
+
+    float* out = rec + (size_t)s * N * N;
+    for (int pr = warp; pr < N / 2; pr += FFT_WARPS) {
+        const int y1 = 2 * pr, y2 = y1 + 1;
+        for (int kx = lane; kx < N; kx += 32) fa[kx] = make_float2(0.f, 0.f);
+        __syncwarp();
+        for (int kx = lane; kx < K1; kx += 32) {
+            const float2 a = C[kx * CP + y1], b = C[kx * CP + y2];
+            fa[kx] = make_float2(a.x - b.y, a.y + b.x);
+            if (kx > 0) fa[N - kx] = make_float2(a.x + b.y, -a.y + b.x);
+        }
+        __syncwarp();
+        const float2* Zr = warp_fft<N, true>(fa, fb, stw, lane);
+        for (int x = lane; x < N; x += 32) {
+            const float2 v = Zr[x];
+            out[(size_t)y1 * N + x] = v.x * scale + mmean * swx[x] * swy[y1];
+            out[(size_t)y2 * N + x] = v.y * scale + mmean * swx[x] * swy[y2];
+        }
+        __syncwarp();
+    }
+}
+
+template <int N>
+cudaError_t spectra_n(const PlanDev& p, const void* frames, int frame_type, int F, int sub0,
+                      int nsub, void* spec, float* flux, float* mu, cudaStream_t st) {
+    const size_t sm = fft_smem(N, p.K);
+    dim3 grid(F, nsub);
+    cudaError_t e = cudaSuccess;
+#define SM_LAUNCH(TIN, PREC)                                                                    \
+    do {                                                                                        \
+        e = cudaFuncSetAttribute(k_spectra<N, TIN, PREC>,                                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);         \
+        if (e != cudaSuccess) return e;                                                         \
+        k_spectra<N, TIN, PREC><<<grid, FFT_THREADS, sm, st>>>(                                 \
+            p, reinterpret_cast<const TIN*>(frames), F, sub0, spec, flux, mu);                  \
+    } while (0)
+    if (frame_type == SM_U16) {
+        if (p.prec == SM_FP32) SM_LAUNCH(uint16_t, SM_FP32);
+        else if (p.prec == SM_FP16) SM_LAUNCH(uint16_t, SM_FP16);
+        else SM_LAUNCH(uint16_t, SM_BF16);
+    } else {
+        if (p.prec == SM_FP32) SM_LAUNCH(float, SM_FP32);
+        else if (p.prec == SM_FP16) SM_LAUNCH(float, SM_FP16);
+        else SM_LAUNCH(float, SM_BF16);
+    }
+#undef SM_LAUNCH
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t inverse_n(const PlanDev& p, int F, int sub0, int nsub, const float* A, const double2* z,
+                      const float* flux, const float* mu, float* rec, cudaStream_t st) {
+    const size_t sm = fft_smem(N, p.K);
+    cudaError_t e = cudaFuncSetAttribute(k_inverse<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    k_inverse<N><<<nsub, FFT_THREADS, sm, st>>>(p, F, sub0, A, z, flux, mu, rec);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace smk {
+
+size_t spectra_smem_bytes(int N, int K) { return fft_smem(N, K); }
+
+cudaError_t launch_spectra(const smi::PlanDev& p, const void* frames, int frame_type, int F,
+                           int sub0, int nsub, void* spec, float* flux, float* mu,
+                           cudaStream_t st) {
+    switch (p.N) {
+        case 64: return spectra_n<64>(p, frames, frame_type, F, sub0, nsub, spec, flux, mu, st);
+        case 128: return spectra_n<128>(p, frames, frame_type, F, sub0, nsub, spec, flux, mu, st);
+        case 256: return spectra_n<256>(p, frames, frame_type, F, sub0, nsub, spec, flux, mu, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_inverse(const smi::PlanDev& p, int F, int sub0, int nsub, const float* A,
+                           const double2* z, const float* flux, const float* mu, float* rec,
+                           cudaStream_t st) {
+    switch (p.N) {
+        case 64: return inverse_n<64>(p, F, sub0, nsub, A, z, flux, mu, rec, st);
+        case 128: return inverse_n<128>(p, F, sub0, nsub, A, z, flux, mu, rec, st);
+        case 256: return inverse_n<256>(p, F, sub0, nsub, A, z, flux, mu, rec, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace smk

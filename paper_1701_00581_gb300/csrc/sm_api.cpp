@@ -1,0 +1,501 @@
+// C ABI: workspace layout, stage entry points, the whole-burst path and the
+// serving engine.  No exception crosses the ABI; every call returns a status.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sm_plan.h"
+
+using namespace smi;
+
+namespace {
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t spec_elem_bytes(int prec) { return prec == SM_FP32 ? 8 : 4; }
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&old_);
+        if (old_ != dev) cudaSetDevice(dev);
+        dev_ = dev;
+    }
+    ~DeviceGuard() {
+        if (old_ != dev_) cudaSetDevice(old_);
+    }
+
+  private:
+    int old_ = 0, dev_ = 0;
+};
+
+int check_lay(const sm_plan* plan, const void* ws, const sm_workspace_layout* lay) {
+    if (!plan || !ws || !lay) { set_error("NULL plan, workspace or layout"); return SM_EINVAL; }
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) {
+        set_error("workspace must be 256-byte aligned"); return SM_EINVAL;
+    }
+    return SM_OK;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+int ret(cudaError_t e, const char* where) { return e == cudaSuccess ? SM_OK : cuda_fail(e, where); }
+
+}  // namespace
+
+extern "C" const char* sm_strerror(int s) {
+    switch (s) {
+        case SM_OK: return "ok";
+        case SM_PENDING: return "pending";
+        case SM_EINVAL: return "invalid argument";
+        case SM_ENOMEM: return "request exceeds the memory budget";
+        case SM_EBUSY: return "no free slot, retry later";
+        case SM_ETIMEDOUT: return "timed out";
+        case SM_ECUDA: return "CUDA error";
+        case SM_ECANCELED: return "cancelled";
+        case SM_ENOTFOUND: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* sm_last_error(void) { return g_last_error.c_str(); }
+
+// Workspace sizing.  The per-chunk buffers are sized for nsub_chunk
+// subfields; rec holds all subfields so the mosaic can run at the end.
+extern "C" int sm_workspace_query(const sm_plan* plan, int F, int nsub_chunk, sm_workspace_layout* lay) {
+    if (!plan || !lay) { set_error("NULL argument"); return SM_EINVAL; }
+    const PlanDev& d = plan->dev;
+    if (F < 1 || F > plan->ch.max_frames) { set_error("F out of range 1..max_frames"); return SM_EINVAL; }
+    if (nsub_chunk < 1 || nsub_chunk > d.n_sub) { set_error("nsub_chunk out of range"); return SM_EINVAL; }
+    const size_t n = (size_t)nsub_chunk;
+    const size_t box = (size_t)d.box_rows * d.box_pitch, hb = (size_t)d.hb_rows * d.box_pitch;
+    size_t o = 0;
+    lay->spec = o; o += al(n * F * box * spec_elem_bytes(d.prec));
+    lay->flux = o; o += al(n * F * sizeof(float));
+    lay->mu = o; o += al(n * F * sizeof(float));
+    lay->P = o; o += al(n * hb * sizeof(float));
+    lay->M = o; o += al(n * hb * sizeof(float2));
+    lay->noise = o; o += al(n * sizeof(float));
+    lay->A = o; o += al(n * hb * sizeof(float));
+    lay->B = o; o += al(n * d.n_tiles * (size_t)TILE_PAIRS * sizeof(float2));
+    lay->z = o; o += al(n * hb * sizeof(double2));
+    lay->rec = o; o += al((size_t)d.n_sub * d.N * d.N * sizeof(float));
+    lay->bytes = o;
+    return SM_OK;
+}
+
+extern "C" int sm_stage_spectra(const sm_plan* plan, const void* frames, int frame_type, int F, int sub0,
+                                int nsub, void* ws, const sm_workspace_layout* lay, void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (!frames) { set_error("frames is NULL"); return SM_EINVAL; }
+    if (frame_type != SM_U16 && frame_type != SM_F32) { set_error("bad frame_type"); return SM_EINVAL; }
+    if (F < 1 || F > plan->ch.max_frames) { set_error("F out of range"); return SM_EINVAL; }
+    if (sub0 < 0 || nsub < 1 || sub0 + nsub > plan->dev.n_sub) { set_error("subfield range"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_spectra(plan->dev, frames, frame_type, F, sub0, nsub, at<void>(ws, lay->spec),
+                                   at<float>(ws, lay->flux), at<float>(ws, lay->mu), (cudaStream_t)stream),
+               "spectra kernel");
+}
+
+extern "C" int sm_stage_stats(const sm_plan* plan, int F, int nsub, void* ws, const sm_workspace_layout* lay,
+                              void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (F < 1 || nsub < 1 || nsub > plan->dev.n_sub) { set_error("bad F or nsub"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_stats(plan->dev, at<void>(ws, lay->spec), F, nsub, at<float>(ws, lay->P),
+                                 at<float2>(ws, lay->M), at<float>(ws, lay->noise), (cudaStream_t)stream),
+               "stats kernel");
+}
+
+extern "C" int sm_stage_amplitude(const sm_plan* plan, int nsub, const double* stf, void* ws,
+                                  const sm_workspace_layout* lay, void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (!stf || nsub < 1 || nsub > plan->dev.n_sub) { set_error("bad stf or nsub"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_amplitude(plan->dev, nsub, stf, at<float>(ws, lay->P), at<float>(ws, lay->noise),
+                                     at<float>(ws, lay->A), (cudaStream_t)stream),
+               "amplitude kernel");
+}
+
+extern "C" int sm_stage_bispectrum(const sm_plan* plan, int F, int nsub, void* ws,
+                                   const sm_workspace_layout* lay, void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (F < 1 || nsub < 1 || nsub > plan->dev.n_sub) { set_error("bad F or nsub"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_bispectrum(plan->dev, at<void>(ws, lay->spec), F, nsub, at<float2>(ws, lay->B),
+                                      (cudaStream_t)stream),
+               "bispectrum kernel");
+}
+
+extern "C" int sm_stage_phase(const sm_plan* plan, int nsub, void* ws, const sm_workspace_layout* lay,
+                              void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (nsub < 1 || nsub > plan->dev.n_sub) { set_error("bad nsub"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_phase(plan->dev, nsub, at<float2>(ws, lay->B), at<float2>(ws, lay->M),
+                                 at<double2>(ws, lay->z), (cudaStream_t)stream),
+               "phase kernel");
+}
+
+extern "C" int sm_stage_inverse(const sm_plan* plan, int F, int sub0, int nsub, void* ws,
+                                const sm_workspace_layout* lay, void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (F < 1 || sub0 < 0 || nsub < 1 || sub0 + nsub > plan->dev.n_sub) { set_error("subfield range"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_inverse(plan->dev, F, sub0, nsub, at<float>(ws, lay->A), at<double2>(ws, lay->z),
+                                   at<float>(ws, lay->flux), at<float>(ws, lay->mu), at<float>(ws, lay->rec),
+                                   (cudaStream_t)stream),
+               "inverse kernel");
+}
+
+extern "C" int sm_stage_mosaic(const sm_plan* plan, void* ws, const sm_workspace_layout* lay, float* out,
+                               uint8_t* valid, void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (!out) { set_error("out is NULL"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_mosaic(plan->dev, at<float>(ws, lay->rec), out, valid, (cudaStream_t)stream),
+               "mosaic kernel");
+}
+
+extern "C" int sm_reconstruct(const sm_plan* plan, const void* frames, int frame_type, int F,
+                              const double* stf, int nsub_chunk, void* ws, const sm_workspace_layout* lay,
+                              float* out, uint8_t* valid, void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    const int n = plan->dev.n_sub;
+    if (nsub_chunk < 1 || nsub_chunk > n) { set_error("nsub_chunk out of range"); return SM_EINVAL; }
+    for (int s0 = 0; s0 < n; s0 += nsub_chunk) {
+        const int ns = std::min(nsub_chunk, n - s0);
+        if ((rc = sm_stage_spectra(plan, frames, frame_type, F, s0, ns, ws, lay, stream))) return rc;
+        if ((rc = sm_stage_stats(plan, F, ns, ws, lay, stream))) return rc;
+        if ((rc = sm_stage_amplitude(plan, ns, stf, ws, lay, stream))) return rc;
+        if ((rc = sm_stage_bispectrum(plan, F, ns, ws, lay, stream))) return rc;
+        if ((rc = sm_stage_phase(plan, ns, ws, lay, stream))) return rc;
+        if ((rc = sm_stage_inverse(plan, F, s0, ns, ws, lay, stream))) return rc;
+    }
+    return sm_stage_mosaic(plan, ws, lay, out, valid, stream);
+}
+
+// ============================================================================
+// Serving engine
+// ============================================================================
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over one device arena (host-side bookkeeping only).
+class Arena {
+  public:
+    void init(char* base, size_t bytes) {
+        base_ = base;
+        free_.clear();
+        free_[0] = bytes;
+    }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = al(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = al(bytes);
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    char* base() const { return base_; }
+
+  private:
+    char* base_ = nullptr;
+    std::map<size_t, size_t> free_;
+};
+
+struct Job {
+    uint64_t ticket = 0;
+    int channel = 0, F = 0, slot = -1;
+    size_t off = 0, bytes = 0;
+    float* host_out = nullptr;
+    uint8_t* host_valid = nullptr;
+    float* d_out = nullptr;
+    uint8_t* d_valid = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    double t_submit = 0.0;
+    int status = SM_PENDING;
+};
+
+}  // namespace
+
+struct sm_handle {
+    sm_config cfg;
+    std::vector<sm_channel> ch;
+    std::vector<sm_plan*> plans;
+    std::vector<int> chunk;               // subfields per chunk, per channel
+    std::vector<cudaStream_t> streams;
+    std::vector<bool> stream_busy;
+    Arena arena;
+    void* dmem = nullptr;
+    std::mutex mu;
+    std::map<uint64_t, Job> jobs;
+    uint64_t next_ticket = 1;
+    Clock::time_point t0;
+};
+
+namespace {
+
+double ms_since(const Clock::time_point& t0) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+// Device bytes one burst of channel c holds: frames, workspace, mosaic, mask, STF.
+size_t burst_bytes(const sm_handle* h, int c, int F, sm_workspace_layout* lay) {
+    const sm_channel& ch = h->ch[c];
+    sm_workspace_query(h->plans[c], F, h->chunk[c], lay);
+    const size_t fb = (size_t)F * ch.W * ch.H * 2;   // uint16 frames
+    return al(lay->bytes) + al(fb * 2) + al((size_t)ch.W * ch.H * 4) + al((size_t)ch.W * ch.H) +
+           al((size_t)ch.N * ch.N * sizeof(double));
+}
+
+void finish_job(sm_handle* h, Job& j) {
+    if (j.ev_start) cudaEventDestroy(j.ev_start);
+    if (j.ev_done) cudaEventDestroy(j.ev_done);
+    j.ev_start = j.ev_done = nullptr;
+    if (j.bytes) h->arena.release(j.off, j.bytes);
+    j.bytes = 0;
+    if (j.slot >= 0) h->stream_busy[j.slot] = false;
+    j.slot = -1;
+}
+
+}  // namespace
+
+extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
+    if (!cfg || !out || cfg->n_channels < 1 || !cfg->ch || cfg->max_inflight < 1) {
+        set_error("bad sm_config"); return SM_EINVAL;
+    }
+    *out = nullptr;
+    sm_handle* h = new (std::nothrow) sm_handle();
+    if (!h) { set_error("host allocation failed"); return SM_ENOMEM; }
+    h->cfg = *cfg;
+    h->ch.assign(cfg->ch, cfg->ch + cfg->n_channels);
+    h->cfg.ch = h->ch.data();
+    h->t0 = Clock::now();
+    DeviceGuard g(cfg->device);
+    for (int c = 0; c < cfg->n_channels; ++c) {
+        sm_plan* p = nullptr;
+        int rc = sm_plan_create(&h->ch[c], cfg->device, &p);
+        if (rc) { for (auto* q : h->plans) sm_plan_destroy(q); delete h; return rc; }
+        h->plans.push_back(p);
+        // chunk: all subfields if one burst of the channel fits its share
+        // of the budget, otherwise the largest count that does
+        const size_t share = cfg->hbm_budget_bytes / (size_t)cfg->max_inflight;
+        int lo = 1, hi = p->dev.n_sub;
+        h->chunk.push_back(hi);
+        sm_workspace_layout lay;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            h->chunk[c] = mid;
+            if (burst_bytes(h, c, h->ch[c].max_frames, &lay) <= share) lo = mid; else hi = mid - 1;
+        }
+        h->chunk[c] = lo;
+    }
+    cudaError_t e = cudaMalloc(&h->dmem, cfg->hbm_budget_bytes);
+    if (e != cudaSuccess) {
+        for (auto* q : h->plans) sm_plan_destroy(q);
+        delete h;
+        return cuda_fail(e, "cudaMalloc(engine arena)");
+    }
+    h->arena.init(static_cast<char*>(h->dmem), cfg->hbm_budget_bytes);
+    for (int i = 0; i < cfg->max_inflight; ++i) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaStreamCreate"); }
+        h->streams.push_back(s);
+        h->stream_busy.push_back(false);
+    }
+    *out = h;
+    return SM_OK;
+}
+
+extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket) {
+    if (!h || !b || !ticket) { set_error("NULL argument"); return SM_EINVAL; }
+    if (b->channel < 0 || b->channel >= (int)h->ch.size()) { set_error("bad channel"); return SM_EINVAL; }
+    const sm_channel& ch = h->ch[b->channel];
+    if (b->F < 1 || b->F > ch.max_frames || !b->frames || !b->out) { set_error("bad burst"); return SM_EINVAL; }
+    if (b->frame_type != SM_U16 && b->frame_type != SM_F32) { set_error("bad frame_type"); return SM_EINVAL; }
+    if (!b->stf && !b->d_over_r0) { set_error("need stf or d_over_r0"); return SM_EINVAL; }
+    std::vector<double> stf;
+    if (!b->stf) {
+        stf.resize((size_t)ch.N * ch.N);
+        int rc = sm_model_stf(&ch, b->F, b->d_over_r0, stf.data());
+        if (rc) return rc;
+    }
+    const double* stf_src = b->stf ? b->stf : stf.data();
+    DeviceGuard g(h->cfg.device);
+    sm_workspace_layout lay;
+    const size_t need = burst_bytes(h, b->channel, b->F, &lay);
+    if (need > h->cfg.hbm_budget_bytes) { set_error("burst exceeds the HBM budget"); return SM_ENOMEM; }
+
+    Job j;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        int slot = -1;
+        for (size_t i = 0; i < h->streams.size(); ++i)
+            if (!h->stream_busy[i]) { slot = (int)i; break; }
+        if (slot < 0) { set_error("all in-flight slots busy"); return SM_EBUSY; }
+        size_t off = 0;
+        if (!h->arena.alloc(need, &off)) { set_error("budget full"); return SM_EBUSY; }
+        h->stream_busy[slot] = true;
+        j.slot = slot;
+        j.off = off;
+        j.bytes = need;
+        j.ticket = h->next_ticket++;
+    }
+    cudaStream_t st = h->streams[j.slot];
+    char* base = h->arena.base() + j.off;
+    void* ws = base;
+    const size_t fbytes = (size_t)b->F * ch.W * ch.H * (b->frame_type == SM_U16 ? 2 : 4);
+    char* d_frames = base + al(lay.bytes);
+    j.d_out = reinterpret_cast<float*>(d_frames + al((size_t)b->F * ch.W * ch.H * 2 * 2));
+    j.d_valid = reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(j.d_out) + al((size_t)ch.W * ch.H * 4));
+    double* d_stf = reinterpret_cast<double*>(reinterpret_cast<char*>(j.d_valid) + al((size_t)ch.W * ch.H));
+    j.channel = b->channel;
+    j.F = b->F;
+    j.host_out = b->out;
+    j.host_valid = b->valid;
+    cudaError_t e = cudaEventCreate(&j.ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&j.ev_done);
+    if (e == cudaSuccess) {
+        if (b->frames_on_device)
+            e = cudaMemcpyAsync(d_frames, b->frames, fbytes, cudaMemcpyDeviceToDevice, st);
+        else
+            e = cudaMemcpyAsync(d_frames, b->frames, fbytes, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_stf, stf_src, (size_t)ch.N * ch.N * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(j.ev_start);   // input staged: caller may reuse frames
+    int rc = SM_OK;
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "staging burst");
+    } else {
+        rc = sm_reconstruct(h->plans[b->channel], d_frames, b->frame_type, b->F, d_stf, h->chunk[b->channel], ws,
+                            &lay, j.d_out, j.d_valid, st);
+        if (rc == SM_OK) {
+            e = cudaEventRecord(j.ev_done, st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
+        }
+    }
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (rc != SM_OK) {
+        cudaStreamSynchronize(st);
+        finish_job(h, j);
+        return rc;
+    }
+    j.t_submit = ms_since(h->t0);
+    *ticket = j.ticket;
+    h->jobs[j.ticket] = j;
+    return SM_OK;
+}
+
+extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result* res) {
+    if (!h) { set_error("NULL handle"); return SM_EINVAL; }
+    const auto start = Clock::now();
+    for (;;) {
+        cudaEvent_t ev = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(h->mu);
+            auto it = h->jobs.find(ticket);
+            if (it == h->jobs.end()) { set_error("unknown ticket"); return SM_ENOTFOUND; }
+            ev = it->second.ev_done;
+        }
+        DeviceGuard g(h->cfg.device);
+        cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) {
+            std::lock_guard<std::mutex> lk(h->mu);
+            auto it = h->jobs.find(ticket);
+            int rc = cuda_fail(q, "burst execution");
+            if (res) { std::memset(res, 0, sizeof(*res)); res->status = rc; }
+            finish_job(h, it->second);
+            h->jobs.erase(it);
+            return rc;
+        }
+        const double waited = std::chrono::duration<double, std::milli>(Clock::now() - start).count();
+        if (timeout_ms == 0 || (timeout_ms > 0 && waited >= timeout_ms)) {
+            if (res) { std::memset(res, 0, sizeof(*res)); res->status = timeout_ms == 0 ? SM_PENDING : SM_ETIMEDOUT; }
+            return timeout_ms == 0 ? SM_PENDING : SM_ETIMEDOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    std::lock_guard<std::mutex> lk(h->mu);
+    auto it = h->jobs.find(ticket);
+    if (it == h->jobs.end()) { set_error("unknown ticket"); return SM_ENOTFOUND; }
+    Job& j = it->second;
+    const double t_done = ms_since(h->t0);
+    DeviceGuard g(h->cfg.device);
+    const sm_channel& ch = h->ch[j.channel];
+    const size_t npx = (size_t)ch.W * ch.H;
+    cudaError_t e = cudaMemcpy(j.host_out, j.d_out, npx * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && j.host_valid) e = cudaMemcpy(j.host_valid, j.d_valid, npx, cudaMemcpyDeviceToHost);
+    float gms = 0.f;
+    cudaEventElapsedTime(&gms, j.ev_start, j.ev_done);
+    int rc = e == cudaSuccess ? SM_OK : cuda_fail(e, "copying the mosaic");
+    if (res) {
+        res->status = rc;
+        res->t_submit_ms = j.t_submit;
+        res->t_done_ms = t_done;
+        res->gpu_ms = gms;
+        res->bytes_admitted = j.bytes;
+    }
+    finish_job(h, j);
+    h->jobs.erase(it);
+    return rc;
+}
+
+extern "C" int sm_close(sm_handle* h) {
+    if (!h) return SM_OK;
+    DeviceGuard g(h->cfg.device);
+    for (auto s : h->streams) cudaStreamSynchronize(s);
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        for (auto& kv : h->jobs) finish_job(h, kv.second);
+        h->jobs.clear();
+    }
+    for (auto s : h->streams) cudaStreamDestroy(s);
+    if (h->dmem) cudaFree(h->dmem);
+    for (auto* p : h->plans) sm_plan_destroy(p);
+    delete h;
+    return SM_OK;
+}

@@ -1,0 +1,72 @@
+// Internal types shared by the host plan builder, the engine and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "speckle.h"
+
+namespace smi {
+
+// Bispectrum tile geometry (Sect. 2 / 3.2 speckle masking): a CTA owns a
+// block of WBX x WBY target frequencies w and a block of VBX x VBY offsets v.
+// Warp q of the CTA owns offset row vy0 + q; lane (wyl, gx) owns the four
+// targets (wx0 + 4 gx + j, wy0 + wyl), j = 0..3, and the eight offsets
+// (vx0 + kk, vy0 + q), kk = 0..7.
+constexpr int WBX = 16, WBY = 8, VBX = 8, VBY = 8;
+constexpr int TILE_W = WBX * WBY;            // 128 targets
+constexpr int TILE_V = VBX * VBY;            // 64 offsets
+constexpr int TILE_PAIRS = TILE_W * TILE_V;  // 8192 (w, v) slots
+constexpr int BISPEC_THREADS = 256;
+
+constexpr float FP16_SCALE = 16384.0f;       // |I_n| <= 1 -> fits half with margin
+constexpr float FP16_INV_SCALE = 1.0f / 16384.0f;
+
+// Everything a kernel needs to know about a plan, passed by value.
+struct PlanDev {
+    int N, logN, K, R;
+    int W, H, stride, taper;
+    int n_sub, nsx, nsy;
+    int box_rows, box_cols, box_pitch, hb_rows;
+    int r2i;                 // floor((fc N)^2): |k|^2 <= r2i  <=>  |k| <= fc N
+    int n_tiles, n_rings, n_points;
+    int n_wbx, n_wby;
+    int prec, weight;
+    const int4* subs;        // [n_sub] x0, y0, w, h
+    const float* winx;       // [n_sub][N] window along x (0 beyond the extent)
+    const float* winy;       // [n_sub][N]
+    const double* winsum;    // [n_sub] sum of the 2-D window
+    const float2* tw;        // [N] exp(-2 pi i k / N)
+    const int4* tiles;       // [n_tiles] wx0, wy0, vx0, vy0
+    const int* ring_start;   // [n_rings + 1]
+    const int2* points;      // [n_points] (wx, wy), ring-ordered
+    const int* wb_start;     // [n_wbx * n_wby + 1] CSR: tiles of each w-block
+    const int* wb_tiles;
+    const double* t0;        // [hb_rows][box_pitch] diffraction OTF on the half box
+};
+
+}  // namespace smi
+
+// ---- kernel launchers (defined in the .cu files) ---------------------------
+namespace smk {
+cudaError_t launch_spectra(const smi::PlanDev& p, const void* frames, int frame_type, int F,
+                           int sub0, int nsub, void* spec, float* flux, float* mu,
+                           cudaStream_t st);
+cudaError_t launch_stats(const smi::PlanDev& p, const void* spec, int F, int nsub, float* P,
+                         float2* M, float* noise, cudaStream_t st);
+cudaError_t launch_amplitude(const smi::PlanDev& p, int nsub, const double* stf, const float* P,
+                             const float* noise, float* A, cudaStream_t st);
+cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, int nsub,
+                              float2* B, cudaStream_t st);
+cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M,
+                         double2* z, cudaStream_t st);
+cudaError_t launch_inverse(const smi::PlanDev& p, int F, int sub0, int nsub, const float* A,
+                           const double2* z, const float* flux, const float* mu, float* rec,
+                           cudaStream_t st);
+cudaError_t launch_mosaic(const smi::PlanDev& p, const float* rec, float* out, uint8_t* valid,
+                          cudaStream_t st);
+size_t spectra_smem_bytes(int N, int K);
+size_t phase_smem_bytes(int hb_rows, int box_pitch);
+}  // namespace smk

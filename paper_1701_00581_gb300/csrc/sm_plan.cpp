@@ -1,0 +1,340 @@
+// Plan construction: every table that depends only on the channel, built on
+// the host in double precision and uploaded once.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sm_plan.h"
+
+namespace smi {
+
+thread_local std::string g_last_error = "";
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* where) {
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return SM_ECUDA;
+}
+
+// Sect. 2: partially overlapping subfields; ragged edge tiles keep their
+// true extent.
+static std::vector<int> tile_starts(int L, int N, int stride) {
+    int n = L <= N ? 1 : (int)std::ceil((double)(L - N) / stride) + 1;
+    std::vector<int> s(n);
+    for (int k = 0; k < n; ++k) s[k] = k * stride;
+    return s;
+}
+
+// Raised-cosine ramps of `taper` px at both ends; the smaller of the two.
+static double tukey_at(int x, int L, int taper) {
+    if (taper <= 0) return 1.0;
+    auto ramp = [&](int q) {
+        return q < taper ? 0.5 * (1.0 - std::cos(M_PI * (q + 0.5) / taper)) : 1.0;
+    };
+    return std::min(ramp(x), ramp(L - 1 - x));
+}
+
+bool pair_used_host(int wx, int wy, int vx, int vy, int r2i, int R2) {
+    const int w2 = wx * wx + wy * wy, v2 = vx * vx + vy * vy;
+    const int ux = wx - vx, uy = wy - vy, u2 = ux * ux + uy * uy;
+    const bool inH = wy > 0 || (wy == 0 && wx > 0);
+    return inH && w2 >= 2 && w2 <= r2i && v2 > 0 && v2 <= R2 && v2 < w2 && u2 < w2;
+}
+
+int validate_channel(const sm_channel* ch) {
+    if (!ch) { set_error("channel is NULL"); return SM_EINVAL; }
+    if (ch->N != 64 && ch->N != 128 && ch->N != 256) {
+        set_error("N must be 64, 128 or 256"); return SM_EINVAL;
+    }
+    if (ch->W < 1 || ch->H < 1 || ch->W > 65536 || ch->H > 65536) {
+        set_error("frame size out of range"); return SM_EINVAL;
+    }
+    if (ch->stride < 1 || ch->stride > ch->N) { set_error("stride must be in 1..N"); return SM_EINVAL; }
+    if (!(ch->fc > 0.0 && ch->fc < 0.5)) { set_error("fc must be in (0, 0.5)"); return SM_EINVAL; }
+    const double r = ch->fc * ch->N;
+    const int K = (int)std::floor(r);
+    if (K < 2) { set_error("cutoff radius fc*N must be >= 2"); return SM_EINVAL; }
+    if (ch->R < 1 || ch->R > K) { set_error("R must be in 1..floor(fc*N)"); return SM_EINVAL; }
+    if (ch->taper < 0 || ch->taper > ch->N / 4) { set_error("taper must be in 0..N/4"); return SM_EINVAL; }
+    if (ch->spectra_prec < SM_FP32 || ch->spectra_prec > SM_BF16) {
+        set_error("spectra_prec must be SM_FP32, SM_FP16 or SM_BF16"); return SM_EINVAL;
+    }
+    if (ch->phase_weight != SM_W_BISPEC && ch->phase_weight != SM_W_UNIT) {
+        set_error("phase_weight must be SM_W_BISPEC or SM_W_UNIT"); return SM_EINVAL;
+    }
+    if (ch->max_frames < 1) { set_error("max_frames must be >= 1"); return SM_EINVAL; }
+    if (!(ch->ck >= 0.0)) { set_error("ck must be >= 0"); return SM_EINVAL; }
+    if (smk::spectra_smem_bytes(ch->N, K) > 227 * 1024) {
+        set_error("fc*N too large for the shared-memory FFT at this N"); return SM_EINVAL;
+    }
+    const int pitch = ((2 * K + 1) + 3) / 4 * 4;
+    if (smk::phase_smem_bytes(K + 1, pitch) > 227 * 1024) {
+        set_error("phase table exceeds shared memory"); return SM_EINVAL;
+    }
+    return SM_OK;
+}
+
+}  // namespace smi
+
+using namespace smi;
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
+    if (!out) { set_error("out is NULL"); return SM_EINVAL; }
+    *out = nullptr;
+    int rc = validate_channel(ch);
+    if (rc != SM_OK) return rc;
+    cudaError_t ce = cudaSetDevice(device);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+
+    sm_plan* pl = new (std::nothrow) sm_plan();
+    if (!pl) { set_error("host allocation failed"); return SM_ENOMEM; }
+    pl->ch = *ch;
+    pl->device = device;
+    const int N = ch->N, R = ch->R;
+    const double r = ch->fc * N;
+    const int K = (int)std::floor(r);
+    const int r2i = (int)std::floor(r * r);
+    PlanDev& d = pl->dev;
+    std::memset(&d, 0, sizeof(d));
+    d.N = N; d.K = K; d.R = R; d.W = ch->W; d.H = ch->H; d.stride = ch->stride; d.taper = ch->taper;
+    d.logN = N == 64 ? 6 : (N == 128 ? 7 : 8);
+    d.r2i = r2i;
+    d.prec = ch->spectra_prec; d.weight = ch->phase_weight;
+    d.box_rows = K + R + 1;
+    d.box_cols = 2 * K + 1;
+    d.box_pitch = (d.box_cols + 3) / 4 * 4;
+    d.hb_rows = K + 1;
+
+    // subfield grid
+    auto xs = tile_starts(ch->W, N, ch->stride), ys = tile_starts(ch->H, N, ch->stride);
+    d.nsx = (int)xs.size(); d.nsy = (int)ys.size(); d.n_sub = d.nsx * d.nsy;
+    pl->subs.resize(d.n_sub);
+    std::vector<float> winx((size_t)d.n_sub * N, 0.f), winy((size_t)d.n_sub * N, 0.f);
+    std::vector<double> winsum(d.n_sub);
+    for (int j = 0; j < d.nsy; ++j)
+        for (int i = 0; i < d.nsx; ++i) {
+            const int s = j * d.nsx + i;
+            const int w = std::min(N, ch->W - xs[i]), h = std::min(N, ch->H - ys[j]);
+            pl->subs[s] = make_int4(xs[i], ys[j], w, h);
+            double sx = 0, sy = 0;
+            for (int x = 0; x < w; ++x) { double v = tukey_at(x, w, ch->taper); winx[(size_t)s * N + x] = (float)v; sx += v; }
+            for (int y = 0; y < h; ++y) { double v = tukey_at(y, h, ch->taper); winy[(size_t)s * N + y] = (float)v; sy += v; }
+            winsum[s] = sx * sy;
+        }
+
+    // twiddles exp(-2 pi i k / N)
+    std::vector<float2> tw(N);
+    for (int k = 0; k < N; ++k)
+        tw[k] = make_float2((float)std::cos(-2.0 * M_PI * k / N), (float)std::sin(-2.0 * M_PI * k / N));
+
+    // diffraction OTF T0 on the half box
+    const size_t hb = (size_t)d.hb_rows * d.box_pitch;
+    std::vector<double> t0(hb, 0.0);
+    int nU = 0;
+    for (int ky = -K; ky <= K; ++ky)
+        for (int kx = -K; kx <= K; ++kx) {
+            const int q = kx * kx + ky * ky;
+            if (q > r2i) continue;
+            ++nU;
+            if (ky < 0) continue;
+            const double rho = std::sqrt((double)q) / r;
+            t0[(size_t)ky * d.box_pitch + kx + K] =
+                rho <= 1.0 ? (2.0 / M_PI) * (std::acos(rho) - rho * std::sqrt(1.0 - rho * rho)) : 0.0;
+        }
+    int nV = 0;
+    for (int vy = -R; vy <= R; ++vy)
+        for (int vx = -R; vx <= R; ++vx)
+            if ((vx | vy) != 0 && vx * vx + vy * vy <= R * R) ++nV;
+    pl->n_U = nU; pl->n_V = nV;
+
+    // bispectrum tiles: every (w-block, v-block) holding a used pair
+    d.n_wbx = (2 * K + 1 + WBX - 1) / WBX;
+    d.n_wby = (K + 1 + WBY - 1) / WBY;
+    pl->n_vbx = (2 * R + 1 + VBX - 1) / VBX;
+    pl->n_vby = (2 * R + 1 + VBY - 1) / VBY;
+    const int nwb = d.n_wbx * d.n_wby, nvb = pl->n_vbx * pl->n_vby;
+    pl->tile_of.assign((size_t)nwb * nvb, -1);
+    std::vector<int> wb_count(nwb, 0);
+    long long npairs = 0;
+    for (int wby = 0; wby < d.n_wby; ++wby)
+        for (int wbx = 0; wbx < d.n_wbx; ++wbx) {
+            const int wb = wby * d.n_wbx + wbx;
+            const int wx0 = -K + WBX * wbx, wy0 = WBY * wby;
+            for (int vby = 0; vby < pl->n_vby; ++vby)
+                for (int vbx = 0; vbx < pl->n_vbx; ++vbx) {
+                    const int vx0 = -R + VBX * vbx, vy0 = -R + VBY * vby;
+                    long long cnt = 0;
+                    for (int a = 0; a < WBY; ++a)
+                        for (int b = 0; b < WBX; ++b)
+                            for (int c = 0; c < VBY; ++c)
+                                for (int e = 0; e < VBX; ++e)
+                                    cnt += pair_used_host(wx0 + b, wy0 + a, vx0 + e, vy0 + c, r2i, R * R);
+                    if (cnt == 0) continue;
+                    npairs += cnt;
+                    pl->tile_of[(size_t)wb * nvb + vby * pl->n_vbx + vbx] = (int)pl->tiles.size();
+                    pl->tiles.push_back(make_int4(wx0, wy0, vx0, vy0));
+                    wb_count[wb]++;
+                }
+        }
+    d.n_tiles = (int)pl->tiles.size();
+    pl->n_pairs = npairs;
+    pl->wb_start.assign(nwb + 1, 0);
+    for (int b = 0; b < nwb; ++b) pl->wb_start[b + 1] = pl->wb_start[b] + wb_count[b];
+    pl->wb_tiles.resize(d.n_tiles);
+    {
+        std::vector<int> fill(pl->wb_start.begin(), pl->wb_start.end() - 1);
+        for (int t = 0; t < d.n_tiles; ++t) {
+            const int4 T = pl->tiles[t];
+            const int wb = (T.y / WBY) * d.n_wbx + (T.x + K) / WBX;
+            pl->wb_tiles[fill[wb]++] = t;
+        }
+    }
+
+    // recursion schedule: points of the half-plane disk with |w|^2 >= 2,
+    // rings of equal |w|^2 in ascending order
+    std::vector<int2> pts;
+    for (int wy = 0; wy <= K; ++wy)
+        for (int wx = -K; wx <= K; ++wx) {
+            const int q = wx * wx + wy * wy;
+            const bool inH = wy > 0 || (wy == 0 && wx > 0);
+            if (inH && q >= 2 && q <= r2i) pts.push_back(make_int2(wx, wy));
+        }
+    std::stable_sort(pts.begin(), pts.end(), [](const int2& a, const int2& b) {
+        return a.x * a.x + a.y * a.y < b.x * b.x + b.y * b.y;
+    });
+    pl->points = pts;
+    pl->ring_start.clear();
+    for (size_t i = 0; i < pts.size(); ++i) {
+        const int q = pts[i].x * pts[i].x + pts[i].y * pts[i].y;
+        if (i == 0 || q != pts[i - 1].x * pts[i - 1].x + pts[i - 1].y * pts[i - 1].y)
+            pl->ring_start.push_back((int)i);
+    }
+    pl->ring_start.push_back((int)pts.size());
+    d.n_points = (int)pts.size();
+    d.n_rings = (int)pl->ring_start.size() - 1;
+
+    // upload all tables in one allocation
+    struct Piece { const void* src; size_t bytes; size_t off; };
+    std::vector<Piece> pcs = {
+        {pl->subs.data(), pl->subs.size() * sizeof(int4), 0},
+        {winx.data(), winx.size() * sizeof(float), 0},
+        {winy.data(), winy.size() * sizeof(float), 0},
+        {winsum.data(), winsum.size() * sizeof(double), 0},
+        {tw.data(), tw.size() * sizeof(float2), 0},
+        {pl->tiles.data(), pl->tiles.size() * sizeof(int4), 0},
+        {pl->ring_start.data(), pl->ring_start.size() * sizeof(int), 0},
+        {pl->points.data(), pl->points.size() * sizeof(int2), 0},
+        {pl->wb_start.data(), pl->wb_start.size() * sizeof(int), 0},
+        {pl->wb_tiles.data(), pl->wb_tiles.size() * sizeof(int), 0},
+        {t0.data(), t0.size() * sizeof(double), 0},
+    };
+    size_t total = 0;
+    for (auto& p : pcs) { p.off = total; total += align256(std::max<size_t>(p.bytes, 1)); }
+    void* dm = nullptr;
+    ce = cudaMalloc(&dm, total);
+    if (ce != cudaSuccess) { delete pl; return cuda_fail(ce, "cudaMalloc(plan tables)"); }
+    for (auto& p : pcs) {
+        if (p.bytes == 0) continue;
+        ce = cudaMemcpy((char*)dm + p.off, p.src, p.bytes, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) { cudaFree(dm); delete pl; return cuda_fail(ce, "cudaMemcpy(plan tables)"); }
+    }
+    pl->dmem = dm;
+    auto at = [&](int i) { return (const void*)((char*)dm + pcs[i].off); };
+    d.subs = (const int4*)at(0);
+    d.winx = (const float*)at(1);
+    d.winy = (const float*)at(2);
+    d.winsum = (const double*)at(3);
+    d.tw = (const float2*)at(4);
+    d.tiles = (const int4*)at(5);
+    d.ring_start = (const int*)at(6);
+    d.points = (const int2*)at(7);
+    d.wb_start = (const int*)at(8);
+    d.wb_tiles = (const int*)at(9);
+    d.t0 = (const double*)at(10);
+    *out = pl;
+    return SM_OK;
+}
+
+extern "C" int sm_plan_destroy(sm_plan* plan) {
+    if (!plan) return SM_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(plan->device);
+    if (plan->dmem) cudaFree(plan->dmem);
+    cudaSetDevice(dev);
+    delete plan;
+    return SM_OK;
+}
+
+extern "C" int sm_plan_get_info(const sm_plan* plan, sm_plan_info* info) {
+    if (!plan || !info) { set_error("NULL argument"); return SM_EINVAL; }
+    const PlanDev& d = plan->dev;
+    info->n_sub = d.n_sub; info->nsx = d.nsx; info->nsy = d.nsy;
+    info->N = d.N; info->K = d.K; info->R = d.R;
+    info->box_rows = d.box_rows; info->box_cols = d.box_cols; info->box_pitch = d.box_pitch;
+    info->hb_rows = d.hb_rows;
+    info->n_tiles = d.n_tiles; info->tile_pairs = TILE_PAIRS;
+    info->n_pairs = plan->n_pairs;
+    info->n_rings = d.n_rings; info->n_points = d.n_points;
+    info->n_U = plan->n_U; info->n_V = plan->n_V;
+    return SM_OK;
+}
+
+extern "C" int sm_plan_subfields(const sm_plan* plan, int* xywh) {
+    if (!plan || !xywh) { set_error("NULL argument"); return SM_EINVAL; }
+    for (int s = 0; s < plan->dev.n_sub; ++s) {
+        xywh[4 * s] = plan->subs[s].x; xywh[4 * s + 1] = plan->subs[s].y;
+        xywh[4 * s + 2] = plan->subs[s].z; xywh[4 * s + 3] = plan->subs[s].w;
+    }
+    return SM_OK;
+}
+
+extern "C" int sm_plan_pair_index(const sm_plan* plan, long long n, const int* wv, long long* idx) {
+    if (!plan || (n > 0 && (!wv || !idx)) || n < 0) { set_error("bad argument"); return SM_EINVAL; }
+    const PlanDev& d = plan->dev;
+    const int K = d.K, R = d.R, nvb = plan->n_vbx * plan->n_vby;
+    for (long long i = 0; i < n; ++i) {
+        const int wx = wv[4 * i], wy = wv[4 * i + 1], vx = wv[4 * i + 2], vy = wv[4 * i + 3];
+        idx[i] = -1;
+        if (!pair_used_host(wx, wy, vx, vy, d.r2i, R * R)) continue;
+        const int wbx = (wx + K) / WBX, wby = wy / WBY;
+        const int vbx = (vx + R) / VBX, vby = (vy + R) / VBY;
+        const int t = plan->tile_of[(size_t)(wby * d.n_wbx + wbx) * nvb + vby * plan->n_vbx + vbx];
+        if (t < 0) continue;
+        const int wl = (wy - wby * WBY) * WBX + (wx + K - wbx * WBX);
+        const int vl = (vy + R - vby * VBY) * VBX + (vx + R - vbx * VBX);
+        idx[i] = (long long)t * TILE_PAIRS + (long long)wl * TILE_V + vl;
+    }
+    return SM_OK;
+}
+
+extern "C" int sm_model_stf(const sm_channel* ch, int F, const double* d_over_r0, double* stf) {
+    if (!ch || !d_over_r0 || !stf || F < 1) { set_error("bad argument"); return SM_EINVAL; }
+    if (!(ch->fc > 0.0) || ch->N < 2) { set_error("bad channel"); return SM_EINVAL; }
+    for (int i = 0; i < F; ++i)
+        if (!(d_over_r0[i] > 0.0)) { set_error("d_over_r0 must be > 0"); return SM_EINVAL; }
+    const int N = ch->N;
+    const double r = ch->fc * N;
+    std::vector<double> acc((size_t)N * N, 0.0);
+    for (int iy = 0; iy < N; ++iy)
+        for (int ix = 0; ix < N; ++ix) {
+            const double ky = iy - N / 2, kx = ix - N / 2;
+            const double rho = std::sqrt(kx * kx + ky * ky) / r;
+            const double t0 = rho <= 1.0 ? (2.0 / M_PI) * (std::acos(rho) - rho * std::sqrt(1.0 - rho * rho)) : 0.0;
+            double s = 0.0;
+            for (int f = 0; f < F; ++f) {
+                const double d = d_over_r0[f];
+                s += t0 * t0 * std::exp(-6.88 * std::pow(rho * d, 5.0 / 3.0)) + ch->ck * t0 / (d * d);
+            }
+            acc[(size_t)iy * N + ix] = s / F;
+        }
+    const double c = acc[(size_t)(N / 2) * N + N / 2];
+    for (size_t i = 0; i < acc.size(); ++i) stf[i] = acc[i] / c;
+    return SM_OK;
+}

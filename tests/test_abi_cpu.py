@@ -1,0 +1,91 @@
+"""CPU-side checks of the C ABI: the library loads, exports what the header
+declares, validates its arguments, and its host-only model STF matches the
+oracle.  No compute call here needs a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import speckle_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "speckle.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1701_00581_gb300 as P
+    from paper_1701_00581_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    return P.load()
+
+
+def test_header_symbols_are_exported(lib):
+    names = _header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in speckle.h but not exported"
+
+
+def test_binding_covers_header():
+    from paper_1701_00581_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == _header_functions()
+
+
+def test_strerror(lib):
+    assert lib.sm_strerror(0) == b"ok"
+    assert lib.sm_strerror(-3) == b"no free slot, retry later"
+    assert lib.sm_strerror(12345) == b"unknown status"
+
+
+@pytest.mark.parametrize("field,value", [
+    ("N", 100), ("N", 512), ("R", 0), ("R", 40), ("fc", 0.0), ("fc", 0.5), ("taper", 40),
+    ("stride", 0), ("spectra_prec", 3), ("phase_weight", 2), ("max_frames", 0), ("W", 0)])
+def test_plan_create_rejects_bad_channels(lib, field, value):
+    from paper_1701_00581_gb300 import Channel
+    ch = Channel(W=256, H=256, N=128, R=16).to_c()
+    setattr(ch, field, value)
+    h = C.c_void_p()
+    assert lib.sm_plan_create(C.byref(ch), 0, C.byref(h)) == -1
+    assert not h.value
+    assert len(lib.sm_last_error()) > 0
+
+
+def test_model_stf_matches_oracle(lib):
+    from paper_1701_00581_gb300 import Channel
+    rng = np.random.default_rng(5)
+    for N, fc, ck in ((64, 0.2885, 0.435), (128, 0.25, 0.3), (256, 0.2885, 0.0)):
+        d = rng.uniform(5, 15, 7)
+        ch = Channel(W=N, H=N, N=N, R=4, fc=fc, ck=ck).to_c()
+        out = np.zeros((N, N))
+        assert lib.sm_model_stf(C.byref(ch), len(d), d.ctypes.data, out.ctypes.data) == 0
+        ref = O.stf_model(N, fc, d, ck)
+        assert np.max(np.abs(out - ref)) < 1e-12
+
+
+def test_model_stf_rejects_bad_input(lib):
+    from paper_1701_00581_gb300 import Channel
+    ch = Channel(W=64, H=64, N=64, R=4).to_c()
+    out = np.zeros((64, 64))
+    d = np.array([5.0, -1.0])
+    assert lib.sm_model_stf(C.byref(ch), 2, d.ctypes.data, out.ctypes.data) == -1
+    assert lib.sm_model_stf(C.byref(ch), 0, d.ctypes.data, out.ctypes.data) == -1
+
+
+def test_null_arguments_are_rejected(lib):
+    from paper_1701_00581_gb300 import _lib
+    lay = _lib.sm_workspace_layout()
+    assert lib.sm_workspace_query(None, 1, 1, C.byref(lay)) == -1
+    assert lib.sm_plan_get_info(None, None) == -1
+    assert lib.sm_stage_bispectrum(None, 1, 1, None, None, None) == -1
+    assert lib.sm_poll(None, 1, 0, None) == -1
+    assert lib.sm_close(None) == 0
+    assert lib.sm_plan_destroy(None) == 0
