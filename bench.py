@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", default="tio2560", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--size", default=None,
+                    help="WxH override (profiling a smaller case of the same kernels)")
     return ap.parse_args()
 
 
@@ -163,6 +165,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- ranks
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (x itself when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -184,6 +203,10 @@ def main():
 
     cfg, N, R = WORKLOADS[args.workload]
     spec = CONFIGS[cfg]
+    if args.size:
+        import dataclasses
+        w, h = (int(x) for x in args.size.lower().split("x"))
+        spec = dataclasses.replace(spec, W=w, H=h)
     b = make_burst(spec, channel=1, burst=rank, device=f"cuda:{local}")
     F = spec.F
     ch = Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=F)
@@ -234,12 +257,10 @@ def main():
     clocks = sampler.stop()
     ms = t0.elapsed_time(t1)
     bisp_ms = statistics.mean(a.elapsed_time(c) for a, c in bev)
-    tmax = torch.tensor([ms], device=dev)
     if world > 1:
         dist.barrier()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    value = world * args.steps / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms, dev)
+    value = whole_job_rate(args.steps, world, ms_max / 1000.0)
 
     # roofline of the dominant kernel (bispectrum): FP32 ALU bound
     triples = info["n_pairs"] * F * n_sub
@@ -293,11 +314,9 @@ def main():
         if world > 1:
             dist.barrier()
         el, lat = serve(args.steps)
-        tt = torch.tensor([el], device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el_max = max_over_ranks(el, dev)
         eng.close()
-        e2e = {"value": world * args.steps / float(tt.item()), "unit": "bursts/s",
+        e2e = {"value": whole_job_rate(args.steps, world, el_max), "unit": "bursts/s",
                "h2d_bytes_per_step": int(b["frames"].nbytes + N * N * 8),
                "d2h_bytes_per_step": int(spec.W * spec.H * 5),
                "latency_ms_p50": 1000 * float(np.percentile(lat, 50)),

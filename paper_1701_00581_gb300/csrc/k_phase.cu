@@ -4,11 +4,15 @@
 // Since arg B(w - v, v) = phi(w - v) + phi(v) - phi(w), each split of a
 // target w into two already known frequencies gives a phasor estimate of
 // exp(i phi(w)).  One CTA per subfield walks the rings of equal |w|^2 in
-// ascending order (points of one ring never depend on each other); warp q
-// takes points q, q + 16, ... of the ring, its lanes sum
-// exp(i(phi(w-v) + phi(v))) conj B over the offsets v in FP32 products and
-// FP64 sums, and lane 0 stores z(w) = S / |S|.  The known phasors live in
-// shared memory (FP32 copy for the products); the FP64 result goes to HBM.
+// ascending order (points of one ring never depend on each other).  The
+// ring's work is a list of (point, bispectrum tile) items; the 16 warps
+// take items round-robin, four at a time so that their B loads are in
+// flight together, and sum exp(i(phi(w-v) + phi(v))) conj B over the 64
+// offsets of the tile (FP32 products, FP64 sums) into one partial per item.
+// Then one thread per point adds its partials in a fixed order and stores
+// z(w) = S / |S|: the result does not depend on scheduling.  The known
+// phasors live in shared memory (FP32 copy for the products); the FP64
+// result goes to HBM.
 #include "sm_internal.h"
 
 namespace {
@@ -34,14 +38,17 @@ __device__ __forceinline__ float2 zget(const float2* zs, int pitch, int K, int k
     return make_float2(t.x, -t.y);
 }
 
+constexpr int PH_UNROLL = 4;          // items in flight per warp
+
 __global__ void __launch_bounds__(PH_THREADS, 1)
 k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         double2* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float2* zs = reinterpret_cast<float2*>(smem);
-    const int sl = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int K = p.K, pitch = p.box_pitch;
     const size_t hb = (size_t)p.hb_rows * pitch;
+    double2* part = reinterpret_cast<double2*>(smem);              // [max_ring_items]
+    float2* zs = reinterpret_cast<float2*>(part + p.max_ring_items); // [hb]
+    const int sl = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     double2* zo = z + (size_t)sl * hb;
     for (int e = tid; e < (int)hb; e += PH_THREADS) zs[e] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -52,9 +59,9 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         const float2 mx = M[(size_t)sl * hb + K + 1];
         const float2 my = M[(size_t)sl * hb + pitch + K];
         double n = hypot((double)mx.x, (double)mx.y);
-        double2 ax = n > 0 ? make_double2(mx.x / n, mx.y / n) : make_double2(1.0, 0.0);
+        const double2 ax = n > 0 ? make_double2(mx.x / n, mx.y / n) : make_double2(1.0, 0.0);
         n = hypot((double)my.x, (double)my.y);
-        double2 ay = n > 0 ? make_double2(my.x / n, my.y / n) : make_double2(1.0, 0.0);
+        const double2 ay = n > 0 ? make_double2(my.x / n, my.y / n) : make_double2(1.0, 0.0);
         zs[K + 1] = make_float2((float)ax.x, (float)ax.y);
         zs[K - 1] = make_float2((float)ax.x, -(float)ax.y);
         zs[pitch + K] = make_float2((float)ay.x, (float)ay.y);
@@ -66,31 +73,52 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
 
     const int R2 = p.R * p.R;
     const bool unit = p.weight == SM_W_UNIT;
+    const float2* Bs = B + (size_t)sl * p.n_tiles * TILE_PAIRS;
     for (int r = 0; r < p.n_rings; ++r) {
-        const int pe = p.ring_start[r + 1];
-        for (int pt = p.ring_start[r] + warp; pt < pe; pt += PH_WARPS) {
-            const int2 w = p.points[pt];
-            const int wbx = (w.x + K) / smi::WBX, wxl = (w.x + K) - wbx * smi::WBX;
-            const int wby = w.y / smi::WBY, wyl = w.y - wby * smi::WBY;
-            const int wb = wby * p.n_wbx + wbx;
-            double sx = 0.0, sy = 0.0;
-            const int t1 = p.wb_start[wb + 1];
-            for (int ti = p.wb_start[wb]; ti < t1; ++ti) {
-                const int t = p.wb_tiles[ti];
-                const int4 Tt = p.tiles[t];
-                const float2* bp = B + (size_t)(sl * p.n_tiles + t) * TILE_PAIRS +
-                                   (wyl * smi::WBX + wxl) * TILE_V;
+        const int i0 = p.ring_items[r], i1 = p.ring_items[r + 1];
+        // (1) every (point, tile) item of the ring: warp-summed phasor terms
+        for (int base = i0 + warp; base < i1; base += PH_WARPS * PH_UNROLL) {
+            float2 bv[PH_UNROLL][2];
+            int2 wq[PH_UNROLL];
+            int4 tq[PH_UNROLL];
+            bool ok[PH_UNROLL][2];
 #pragma unroll
-                for (int h = 0; h < TILE_V / 32; ++h) {
+            for (int q = 0; q < PH_UNROLL; ++q) {
+                const int it = base + q * PH_WARPS;
+                ok[q][0] = ok[q][1] = false;
+                bv[q][0] = bv[q][1] = make_float2(0.f, 0.f);
+                if (it < i1) {
+                    const int2 item = p.items[it];
+                    const int2 w = p.points[item.x];
+                    const int4 T = p.tiles[item.y];
+                    wq[q] = w;
+                    tq[q] = T;
+                    const int wxl = (w.x + K) % smi::WBX, wyl = w.y % smi::WBY;
+                    const float2* bp = Bs + (size_t)item.y * TILE_PAIRS + (wyl * smi::WBX + wxl) * TILE_V;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int vl = lane + 32 * h;
+                        ok[q][h] = pair_used(w.x, w.y, T.z + (vl % smi::VBX), T.w + (vl / smi::VBX), p.r2i, R2);
+                        if (ok[q][h]) bv[q][h] = bp[vl];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PH_UNROLL; ++q) {
+                const int it = base + q * PH_WARPS;
+                if (it >= i1) break;                       // warp-uniform
+                double sx = 0.0, sy = 0.0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!ok[q][h]) continue;
                     const int vl = lane + 32 * h;
-                    const int vx = Tt.z + (vl % smi::VBX), vy = Tt.w + (vl / smi::VBX);
-                    if (!pair_used(w.x, w.y, vx, vy, p.r2i, R2)) continue;
-                    const float2 b = bp[vl];
-                    const float2 zu = zget(zs, pitch, K, w.x - vx, w.y - vy);
+                    const int vx = tq[q].z + (vl % smi::VBX), vy = tq[q].w + (vl / smi::VBX);
+                    const float2 b = bv[q][h];
+                    const float2 zu = zget(zs, pitch, K, wq[q].x - vx, wq[q].y - vy);
                     const float2 zv = zget(zs, pitch, K, vx, vy);
-                    const float2 q = make_float2(zu.x * zv.x - zu.y * zv.y, zu.x * zv.y + zu.y * zv.x);
-                    float tx = q.x * b.x + q.y * b.y;      // q * conj(b)
-                    float ty = q.y * b.x - q.x * b.y;
+                    const float2 c = make_float2(zu.x * zv.x - zu.y * zv.y, zu.x * zv.y + zu.y * zv.x);
+                    float tx = c.x * b.x + c.y * b.y;      // c * conj(b)
+                    float ty = c.y * b.x - c.x * b.y;
                     if (unit) {
                         const float m = sqrtf(b.x * b.x + b.y * b.y);
                         if (m > 0.f) {
@@ -103,22 +131,33 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
                     sx += tx;
                     sy += ty;
                 }
-            }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            }
-            if (lane == 0) {
-                const double n = hypot(sx, sy);
-                const double2 zz = n > 0 ? make_double2(sx / n, sy / n) : make_double2(1.0, 0.0);
-                const int o = w.y * pitch + w.x + K;
-                zs[o] = make_float2((float)zz.x, (float)zz.y);
-                zo[o] = zz;
-                if (w.y == 0) {
-                    zs[-w.x + K] = make_float2((float)zz.x, -(float)zz.y);
-                    zo[-w.x + K] = make_double2(zz.x, -zz.y);
+                for (int o = 16; o > 0; o >>= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
                 }
+                if (lane == 0) part[it - i0] = make_double2(sx, sy);
+            }
+        }
+        __syncthreads();
+        // (2) one thread per point: sum its items in order, normalise
+        const int pe = p.ring_start[r + 1];
+        for (int pt = p.ring_start[r] + tid; pt < pe; pt += PH_THREADS) {
+            double sx = 0.0, sy = 0.0;
+            const int a0 = p.point_items[pt], a1 = p.point_items[pt + 1];
+            for (int a = a0; a < a1; ++a) {
+                sx += part[a - i0].x;
+                sy += part[a - i0].y;
+            }
+            const int2 w = p.points[pt];
+            const double n = hypot(sx, sy);
+            const double2 zz = n > 0 ? make_double2(sx / n, sy / n) : make_double2(1.0, 0.0);
+            const int o = w.y * pitch + w.x + K;
+            zs[o] = make_float2((float)zz.x, (float)zz.y);
+            zo[o] = zz;
+            if (w.y == 0) {
+                zs[-w.x + K] = make_float2((float)zz.x, -(float)zz.y);
+                zo[-w.x + K] = make_double2(zz.x, -zz.y);
             }
         }
         __syncthreads();
@@ -129,13 +168,13 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
 
 namespace smk {
 
-size_t phase_smem_bytes(int hb_rows, int box_pitch) {
-    return (size_t)hb_rows * box_pitch * sizeof(float2);
+size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items) {
+    return (size_t)max_ring_items * sizeof(double2) + (size_t)hb_rows * box_pitch * sizeof(float2);
 }
 
 cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M,
                          double2* z, cudaStream_t st) {
-    const size_t sm = phase_smem_bytes(p.hb_rows, p.box_pitch);
+    const size_t sm = phase_smem_bytes(p.hb_rows, p.box_pitch, p.max_ring_items);
     cudaError_t e = cudaFuncSetAttribute(k_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_phase<<<nsub, PH_THREADS, sm, st>>>(p, B, M, z);

@@ -44,6 +44,12 @@ struct PlanDev {
     const int2* points;      // [n_points] (wx, wy), ring-ordered
     const int* wb_start;     // [n_wbx * n_wby + 1] CSR: tiles of each w-block
     const int* wb_tiles;
+    // phase recursion work items: (point, tile) pairs holding at least one
+    // pair the point reads, grouped by point, points in ring order
+    const int2* items;          // [n_items] (point index, tile id)
+    const int* ring_items;      // [n_rings + 1] first item of each ring
+    const int* point_items;     // [n_points + 1] first item of each point
+    int n_items, max_ring_items;
     const double* t0;        // [hb_rows][box_pitch] diffraction OTF on the half box
 };
 
@@ -68,5 +74,5 @@ cudaError_t launch_inverse(const smi::PlanDev& p, int F, int sub0, int nsub, con
 cudaError_t launch_mosaic(const smi::PlanDev& p, const float* rec, float* out, uint8_t* valid,
                           cudaStream_t st);
 size_t spectra_smem_bytes(int N, int K);
-size_t phase_smem_bytes(int hb_rows, int box_pitch);
+size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items);
 }  // namespace smk

@@ -72,7 +72,7 @@ int validate_channel(const sm_channel* ch) {
         set_error("fc*N too large for the shared-memory FFT at this N"); return SM_EINVAL;
     }
     const int pitch = ((2 * K + 1) + 3) / 4 * 4;
-    if (smk::phase_smem_bytes(K + 1, pitch) > 227 * 1024) {
+    if (smk::phase_smem_bytes(K + 1, pitch, 0) > 200 * 1024) {
         set_error("phase table exceeds shared memory"); return SM_EINVAL;
     }
     return SM_OK;
@@ -219,6 +219,38 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.n_points = (int)pts.size();
     d.n_rings = (int)pl->ring_start.size() - 1;
 
+    // recursion work items: for each point (ring order), the tiles of its
+    // w-block that hold at least one pair the point reads
+    pl->point_items.assign(d.n_points + 1, 0);
+    pl->items.clear();
+    for (int pi = 0; pi < d.n_points; ++pi) {
+        const int wx = pts[pi].x, wy = pts[pi].y;
+        const int wb = (wy / WBY) * d.n_wbx + (wx + K) / WBX;
+        pl->point_items[pi] = (int)pl->items.size();
+        for (int ti = pl->wb_start[wb]; ti < pl->wb_start[wb + 1]; ++ti) {
+            const int t = pl->wb_tiles[ti];
+            const int4 T = pl->tiles[t];
+            bool any = false;
+            for (int c = 0; c < VBY && !any; ++c)
+                for (int e = 0; e < VBX && !any; ++e)
+                    any = pair_used_host(wx, wy, T.z + e, T.w + c, r2i, R * R);
+            if (any) pl->items.push_back(make_int2(pi, t));
+        }
+    }
+    pl->point_items[d.n_points] = (int)pl->items.size();
+    pl->ring_items.resize(d.n_rings + 1);
+    d.max_ring_items = 0;
+    for (int rr = 0; rr <= d.n_rings; ++rr) {
+        pl->ring_items[rr] = pl->point_items[pl->ring_start[rr]];
+        if (rr > 0) d.max_ring_items = std::max(d.max_ring_items, pl->ring_items[rr] - pl->ring_items[rr - 1]);
+    }
+    d.n_items = (int)pl->items.size();
+    if (smk::phase_smem_bytes(d.hb_rows, d.box_pitch, d.max_ring_items) > 227 * 1024) {
+        delete pl;
+        set_error("phase recursion tables exceed shared memory");
+        return SM_EINVAL;
+    }
+
     // upload all tables in one allocation
     struct Piece { const void* src; size_t bytes; size_t off; };
     std::vector<Piece> pcs = {
@@ -233,6 +265,9 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         {pl->wb_start.data(), pl->wb_start.size() * sizeof(int), 0},
         {pl->wb_tiles.data(), pl->wb_tiles.size() * sizeof(int), 0},
         {t0.data(), t0.size() * sizeof(double), 0},
+        {pl->items.data(), pl->items.size() * sizeof(int2), 0},
+        {pl->ring_items.data(), pl->ring_items.size() * sizeof(int), 0},
+        {pl->point_items.data(), pl->point_items.size() * sizeof(int), 0},
     };
     size_t total = 0;
     for (auto& p : pcs) { p.off = total; total += align256(std::max<size_t>(p.bytes, 1)); }
@@ -257,6 +292,9 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.wb_start = (const int*)at(8);
     d.wb_tiles = (const int*)at(9);
     d.t0 = (const double*)at(10);
+    d.items = (const int2*)at(11);
+    d.ring_items = (const int*)at(12);
+    d.point_items = (const int*)at(13);
     *out = pl;
     return SM_OK;
 }
