@@ -5,20 +5,19 @@
 //
 // with w in the upper half plane, 0 < |v| <= R, |v| < |w| and |w - v| < |w|.
 //
-// Work decomposition: a CTA owns a tile = 16 x 8 targets w x 8 x 8 offsets v
+// Work decomposition: a CTA owns a tile = 16 x 8 targets w x 8 x 4 offsets v
 // of one subfield.  Warp q owns offset row vy0 + q; lane (wyl, gx) owns
 // targets (wx0 + 4 gx + j, wy0 + wyl), j = 0..3, and offsets
 // (vx0 + kk, vy0 + q), kk = 0..7: 32 complex accumulators in registers for
 // the whole burst.  Per frame the CTA stages three rectangles of the frame
-// spectrum in shared memory: the targets W (8 x 16), the offsets V (8 x 8)
-// and U = W - V (15 x 23).  For its 32 pairs a thread reads 4 values of W,
+// spectrum in shared memory: the targets W (8 x 16), the offsets V (4 x 8)
+// and U = W - V (11 x 23).  For its 32 pairs a thread reads 4 values of W,
 // 8 broadcast values of V and an 11-wide sliding window of U, so each
 // triple product costs 8 FP32 FMA-pipe instructions and ~0.7 shared loads.
 // The next frame's rectangles are prefetched into registers while the
-// current frame is multiplied out.  Warps none of whose pairs is used skip
-// the arithmetic.  Accumulators are written once per burst.
-#include <cstdlib>
-
+// current frame is multiplied out.  A warp skips the offset columns (and so
+// whole tiles) in which none of its lanes owns a used pair.  Accumulators are
+// written once per burst.
 #include "sm_internal.h"
 
 namespace {
@@ -34,11 +33,11 @@ constexpr int UR = smi::WBY + smi::VBY - 1;     // 15 rows of U
 constexpr int UC = smi::WBX + smi::VBX - 1;     // 23 cols of U
 constexpr int OFF_W = 0;
 constexpr int OFF_V = smi::WBY * PW;                      // 136
-constexpr int OFF_U = OFF_V + smi::VBY * smi::VBX;        // 200
-constexpr int BUF = OFF_U + UR * PU;                      // 575 float2 per frame buffer
-constexpr int NLOAD = smi::WBY * smi::WBX + smi::VBY * smi::VBX + UR * UC;  // 537
+constexpr int OFF_U = OFF_V + smi::VBY * smi::VBX;        // 168
+constexpr int BUF = OFF_U + UR * PU;                      // 443 float2 per frame buffer
+constexpr int NLOAD = smi::WBY * smi::WBX + smi::VBY * smi::VBX + UR * UC;  // 413
 constexpr int THREADS = smi::BISPEC_THREADS;
-constexpr int LPT = (NLOAD + THREADS - 1) / THREADS;      // 3 elements per thread
+constexpr int LPT = (NLOAD + THREADS - 1) / THREADS;      // 4 elements per thread
 
 // Bank check (64-bit accesses, half-warp phases): lanes 0..15 hold
 // wyl = 0..3, gx = 0..3 and read element wyl*P + 4*gx + m; with P = 17 or
@@ -66,7 +65,7 @@ __device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, 4)
 k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict__ B) {
     __shared__ __align__(16) float2 S[2 * BUF];
     const int tile = blockIdx.x, sl = blockIdx.y;
@@ -99,15 +98,19 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
         src[i] = inbox ? (ky + p.R) * p.box_pitch + (kx + p.K) : -1;
     }
 
-    // Does this warp own any used pair?
-    bool mine = false;
+    // Offset columns kk for which some lane of this warp owns a used pair:
+    // a warp-uniform mask, so the warp skips columns (and whole tiles) it
+    // does not need without diverging.
+    unsigned kkmask = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int kk = 0; kk < smi::VBX; ++kk) {
+        bool mine = false;
 #pragma unroll
-        for (int kk = 0; kk < smi::VBX; ++kk)
-            mine |= pair_used(wx0 + 4 * gx + j, wy0 + wyl, vx0 + kk, vy0 + warp, p.r2i,
-                              p.R * p.R);
-    const bool active = __any_sync(0xffffffffu, mine);
+        for (int j = 0; j < 4; ++j)
+            mine |= pair_used(wx0 + 4 * gx + j, wy0 + wyl, vx0 + kk, vy0 + warp, p.r2i, p.R * p.R);
+        if (__any_sync(0xffffffffu, mine)) kkmask |= 1u << kk;
+    }
+    const bool active = kkmask != 0;
 
     const size_t box = (size_t)p.box_rows * p.box_pitch;
     const size_t sbase = (size_t)sl * F * box;
@@ -148,6 +151,7 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
             const float2* vp = Sb + OFF_V + warp * smi::VBX;
 #pragma unroll
             for (int kk = 0; kk < smi::VBX; ++kk) {
+                if (!(kkmask & (1u << kk))) continue;    // warp-uniform
                 const float2 b = vp[kk];                 // I(v), warp broadcast
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -176,187 +180,6 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
 }
 
 
-// ---------------------------------------------------------------------------
-// Packed-FP32 variant: the same pairs, tiles and accumulation order, with two
-// triple products per instruction (fma.rn.f32x2 / mul.rn.f32x2 on register
-// pairs).  The FMA pipe's FLOP rate is unchanged, but each triple takes four
-// issue slots instead of eight, which leaves room for the shared loads and
-// the barrier.  Operands are staged as quads (re[x], re[x+1], im[x], im[x+1])
-// so that the pair of neighbouring targets j, j+1 of a thread reads one
-// aligned register pair per component.
-// ---------------------------------------------------------------------------
-typedef unsigned long long f2x;
-
-__device__ __forceinline__ f2x pk(float lo, float hi) {
-    f2x r;
-    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk(f2x v, float& lo, float& hi) {
-    asm("mov.b64 {%0,%1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
-    f2x r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
-    f2x r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
-constexpr int P4 = 25;                              // U quad row pitch (== 1 mod 8)
-constexpr int UQ = UC - 1;                          // 22 quads per U row
-constexpr int PW2 = 9;                              // W quad row pitch
-constexpr int WQ = smi::WBX / 2;                    // 8 quads per W row
-constexpr int Q_U = 0;                              // offsets in float4 units
-constexpr int Q_W = Q_U + UR * P4;                  // 375
-constexpr int Q_V = Q_W + smi::WBY * PW2;           // 447
-constexpr int Q_N = Q_V + smi::VBY * smi::VBX;      // 511 (float4 slots hold 2 float2 each)
-constexpr int QBUF = Q_N + smi::VBY * smi::VBX / 2; // 543 float4 per frame buffer
-constexpr int NT_U = UR * UQ;                       // 330 staging tasks
-constexpr int NT_W = smi::WBY * WQ;                 // 64
-constexpr int NT_V = smi::VBY * smi::VBX;           // 64
-constexpr int NTASK = NT_U + NT_W + NT_V;           // 458
-constexpr int TPT = (NTASK + THREADS - 1) / THREADS;  // 2
-
-template <int PREC>
-__global__ void __launch_bounds__(THREADS, 2)
-k_bispectrum_x2(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict__ B) {
-    __shared__ __align__(16) float4 S[2 * QBUF];
-    const int tile = blockIdx.x, sl = blockIdx.y;
-    const int4 T = p.tiles[tile];
-    const int wx0 = T.x, wy0 = T.y, vx0 = T.z, vy0 = T.w;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // lane -> (gx, wyl) so that each 8-lane shared-memory phase hits 8 distinct quads
-    const int gx = 2 * (lane >> 4) + ((lane >> 2) & 1);
-    const int wyl = 4 * ((lane >> 3) & 1) + (lane & 3);
-
-    // staging tasks: a task fills one quad (two elements) or one V entry
-    int srcA[TPT], srcB[TPT], dst[TPT];
-#pragma unroll
-    for (int i = 0; i < TPT; ++i) {
-        const int e = tid + i * THREADS;
-        int kx = 0, ky = 0, d = -1, two = 1;
-        if (e < NT_U) {
-            const int r = e / UQ, c = e - r * UQ;
-            kx = wx0 - vx0 - (smi::VBX - 1) + c; ky = wy0 - vy0 - (smi::VBY - 1) + r;
-            d = Q_U + r * P4 + c;
-        } else if (e < NT_U + NT_W) {
-            const int e2 = e - NT_U, r = e2 / WQ, q = e2 - r * WQ;
-            kx = wx0 + 2 * q; ky = wy0 + r;
-            d = Q_W + r * PW2 + q;
-        } else if (e < NTASK) {
-            const int e2 = e - NT_U - NT_W, r = e2 / smi::VBX, c = e2 - r * smi::VBX;
-            kx = vx0 + c; ky = vy0 + r;
-            d = Q_V + e2;
-            two = 0;
-        }
-        dst[i] = d | (two << 30);
-        const bool rowin = d >= 0 && ky >= -p.R && ky <= p.K;
-        const int base = (ky + p.R) * p.box_pitch + p.K;
-        srcA[i] = rowin && kx >= -p.K && kx <= p.K ? base + kx : -1;
-        srcB[i] = rowin && two && kx + 1 >= -p.K && kx + 1 <= p.K ? base + kx + 1 : -1;
-    }
-
-    bool mine = false;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int kk = 0; kk < smi::VBX; ++kk)
-            mine |= pair_used(wx0 + 4 * gx + j, wy0 + wyl, vx0 + kk, vy0 + warp, p.r2i, p.R * p.R);
-    const bool active = __any_sync(0xffffffffu, mine);
-
-    const size_t box = (size_t)p.box_rows * p.box_pitch;
-    const size_t sbase = (size_t)sl * F * box;
-    float2 pa[TPT], pb[TPT];
-    auto fetch = [&](size_t fb) {
-#pragma unroll
-        for (int i = 0; i < TPT; ++i) {
-            pa[i] = srcA[i] >= 0 ? load_spec<PREC>(spec, fb + srcA[i]) : make_float2(0.f, 0.f);
-            pb[i] = srcB[i] >= 0 ? load_spec<PREC>(spec, fb + srcB[i]) : make_float2(0.f, 0.f);
-        }
-    };
-    fetch(sbase);
-
-    f2x accr[2][smi::VBX], acci[2][smi::VBX];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int kk = 0; kk < smi::VBX; ++kk) accr[h][kk] = acci[h][kk] = 0ull;
-
-    for (int f = 0; f < F; ++f) {
-        float4* Sb = S + (f & 1) * QBUF;
-#pragma unroll
-        for (int i = 0; i < TPT; ++i) {
-            const int d = dst[i] & 0x3fffffff;
-            if (dst[i] < 0) continue;
-            if (dst[i] >> 30) {
-                Sb[d] = make_float4(pa[i].x, pb[i].x, pa[i].y, pb[i].y);
-            } else {
-                Sb[d] = make_float4(pa[i].x, pa[i].x, pa[i].y, pa[i].y);
-                reinterpret_cast<float2*>(Sb + Q_N)[d - Q_V] = make_float2(-pa[i].y, -pa[i].y);
-            }
-        }
-        __syncthreads();
-        if (f + 1 < F) fetch(sbase + (size_t)(f + 1) * box);
-        if (active) {
-            f2x wr[2], wi[2], nwi[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float4 t = Sb[Q_W + wyl * PW2 + 2 * gx + h];   // targets j = 2h, 2h+1
-                wr[h] = pk(t.x, t.y);
-                wi[h] = pk(t.z, t.w);
-                nwi[h] = pk(-t.z, -t.w);
-            }
-            const float4* urow = Sb + Q_U + (wyl - warp + smi::VBY - 1) * P4 + 4 * gx;
-            const float4* vrow = Sb + Q_V + warp * smi::VBX;
-            const float2* nrow = reinterpret_cast<const float2*>(Sb + Q_N) + warp * smi::VBX;
-#pragma unroll
-            for (int kk = 0; kk < smi::VBX; ++kk) {
-                const float4 bv = vrow[kk];
-                const float2 bn = nrow[kk];
-                const f2x br = pk(bv.x, bv.y), bi = pk(bv.z, bv.w), nbi = pk(bn.x, bn.y);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float4 u = urow[2 * h + 7 - kk];          // I(w - v) for j = 2h, 2h+1
-                    const f2x ur = pk(u.x, u.y), ui = pk(u.z, u.w);
-                    const f2x pr = fma2(ui, nbi, mul2(ur, br));      // Re I(w-v) I(v)
-                    const f2x pi = fma2(ui, br, mul2(ur, bi));       // Im I(w-v) I(v)
-                    accr[h][kk] = fma2(pi, wi[h], fma2(pr, wr[h], accr[h][kk]));
-                    acci[h][kk] = fma2(pr, nwi[h], fma2(pi, wr[h], acci[h][kk]));
-                }
-            }
-        }
-    }
-
-    if (!active) return;
-    const float sc = 1.0f / (float)F;
-    float2* out = B + (size_t)(sl * p.n_tiles + tile) * TILE_PAIRS;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float r0[smi::VBX], r1[smi::VBX], i0[smi::VBX], i1[smi::VBX];
-#pragma unroll
-        for (int kk = 0; kk < smi::VBX; ++kk) {
-            upk(accr[h][kk], r0[kk], r1[kk]);
-            upk(acci[h][kk], i0[kk], i1[kk]);
-        }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int j = 2 * h + e;
-            float4* o = reinterpret_cast<float4*>(out + (wyl * smi::WBX + 4 * gx + j) * TILE_V +
-                                                  warp * smi::VBX);
-#pragma unroll
-            for (int q = 0; q < smi::VBX / 2; ++q)
-                o[q] = e == 0 ? make_float4(r0[2 * q] * sc, i0[2 * q] * sc, r0[2 * q + 1] * sc,
-                                            i0[2 * q + 1] * sc)
-                              : make_float4(r1[2 * q] * sc, i1[2 * q] * sc, r1[2 * q + 1] * sc,
-                                            i1[2 * q + 1] * sc);
-        }
-    }
-}
-
 }  // namespace
 
 namespace smk {
@@ -364,19 +187,9 @@ namespace smk {
 cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, int nsub, float2* B,
                               cudaStream_t st) {
     dim3 grid(p.n_tiles, nsub);
-    static const bool scalar = [] {
-        const char* e = getenv("SPECKLE_BISPECTRUM_SCALAR");
-        return e != nullptr && e[0] == '1';
-    }();
-    if (scalar) {
-        if (p.prec == SM_FP32) k_bispectrum<SM_FP32><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-        else if (p.prec == SM_FP16) k_bispectrum<SM_FP16><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-        else k_bispectrum<SM_BF16><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-    } else {
-        if (p.prec == SM_FP32) k_bispectrum_x2<SM_FP32><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-        else if (p.prec == SM_FP16) k_bispectrum_x2<SM_FP16><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-        else k_bispectrum_x2<SM_BF16><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-    }
+    if (p.prec == SM_FP32) k_bispectrum<SM_FP32><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+    else if (p.prec == SM_FP16) k_bispectrum<SM_FP16><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+    else k_bispectrum<SM_BF16><<<grid, THREADS, 0, st>>>(p, spec, F, B);
     return cudaGetLastError();
 }
 

@@ -2,10 +2,13 @@
 // inverse transform of modulus and phase (Sect. 2, Sect. 3.2).
 //
 // One CTA per (frame, subfield): the tile is cut from the frame, apodised by
-// the separable window, its windowed mean is subtracted, and the 2-D DFT is
+// the separable window, its windowed mean is removed, and the 2-D DFT is
 // taken as real row FFTs (two rows packed per complex FFT) followed by
 // column FFTs of only the K+1 non-negative columns inside the cutoff box.
-// Each FFT is a radix-2 Stockham transform run by one warp in shared memory.
+// The forward transforms are four-step FFTs (N = P x Q) computed in
+// registers by groups of 16 threads with one shared-memory exchange; the
+// inverse (one CTA per subfield, off the critical path) uses warp-wide
+// radix-2 Stockham FFTs in shared memory.
 #include "sm_internal.h"
 
 namespace {
@@ -42,6 +45,77 @@ __device__ __forceinline__ float2* warp_fft(float2* a, float2* b, const float2* 
     return a;
 }
 
+// In-register radix-2 FFT of length L (decimation in time, bit-reversed
+// input order resolved at compile time).  tw[m] = exp(-2 pi i m / N) for the
+// transform size N of the kernel; W_L^k = tw[k N / L].  INV conjugates.
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+template <int L, int N, bool INV>
+__device__ __forceinline__ void reg_fft(float2 (&v)[L], const float2* tw) {
+    constexpr int LB = ilog2(L);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const int j = bitrev(i, LB);
+        if (j > i) {
+            const float2 t = v[i];
+            v[i] = v[j];
+            v[j] = t;
+        }
+    }
+#pragma unroll
+    for (int len = 2; len <= L; len <<= 1) {
+        const int half = len / 2;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            float2 w = tw[j * (N / len)];
+            if (INV) w.y = -w.y;
+#pragma unroll
+            for (int i = 0; i < L; i += len) {
+                const float2 a = v[i + j];
+                const float2 b = v[i + j + half];
+                const float2 t = j == 0 ? b : cmul(b, w);
+                v[i + j] = make_float2(a.x + t.x, a.y + t.y);
+                v[i + j + half] = make_float2(a.x - t.x, a.y - t.y);
+            }
+        }
+    }
+}
+
+// Four-step split of an N-point transform: N = P * Q, thread n1 < P of a
+// group holds x[n1 + P n2] (n2 < Q) on entry; on exit thread k2 < Q holds
+// X[k2 + Q k1] (k1 < P) in out[].  T is the group's [Q][P+1] exchange tile.
+template <int N> struct Split;
+template <> struct Split<64> { static constexpr int P = 8, Q = 8; };
+template <> struct Split<128> { static constexpr int P = 8, Q = 16; };
+template <> struct Split<256> { static constexpr int P = 16, Q = 16; };
+
+template <int N, bool INV>
+__device__ __forceinline__ void four_step(float2 (&v)[Split<N>::Q], float2 (&out)[Split<N>::P],
+                                          float2* T, const float2* tw, int g) {
+    constexpr int P = Split<N>::P, Q = Split<N>::Q;
+    if (g < P) {
+        reg_fft<Q, N, INV>(v, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+            float2 w = tw[g * k2];
+            if (INV) w.y = -w.y;
+            T[k2 * (P + 1) + g] = k2 == 0 ? v[k2] : cmul(v[k2], w);
+        }
+    }
+    __syncwarp();
+    if (g < Q) {
+#pragma unroll
+        for (int n1 = 0; n1 < P; ++n1) out[n1] = T[g * (P + 1) + n1];
+        reg_fft<P, N, INV>(out, tw);
+    }
+    __syncwarp();
+}
+
 __device__ __forceinline__ float load_sample(const uint16_t* p) { return (float)__ldg(p); }
 __device__ __forceinline__ float load_sample(const float* p) { return __ldg(p); }
 
@@ -60,29 +134,57 @@ __device__ __forceinline__ void store_spec(void* spec, size_t idx, float2 v) {
 constexpr int FFT_THREADS = 256;
 constexpr int FFT_WARPS = FFT_THREADS / 32;
 
+// Thread groups of the four-step transform: G threads per transform.
+template <int N> struct Grp {
+    static constexpr int P = Split<N>::P, Q = Split<N>::Q;
+    static constexpr int G = P > Q ? P : Q;
+    static constexpr int NG = FFT_THREADS / G;                       // groups per CTA
+    static constexpr int TB = (Q * (P + 1) > N ? Q * (P + 1) : N);   // exchange buffer
+};
+
+// scratch area (float2): per-warp ping-pong of the inverse, per-group
+// exchange tiles of the forward transform
+template <int N>
+__host__ __device__ constexpr int scratch_elems() {
+    return FFT_WARPS * 2 * N > Grp<N>::NG * Grp<N>::TB ? FFT_WARPS * 2 * N : Grp<N>::NG * Grp<N>::TB;
+}
+__host__ __device__ constexpr int scratch_elems_rt(int N) {
+    return N == 64 ? scratch_elems<64>() : (N == 128 ? scratch_elems<128>() : scratch_elems<256>());
+}
+
 __host__ __device__ constexpr size_t fft_smem(int N, int K) {
     return (size_t)(K + 1) * (N + 1) * sizeof(float2)        // column buffer
-           + (size_t)FFT_WARPS * 2 * N * sizeof(float2)      // per-warp ping-pong
+           + (size_t)scratch_elems_rt(N) * sizeof(float2)    // scratch
            + (size_t)N * sizeof(float2)                      // twiddles
+           + (size_t)(K + 1) * sizeof(float2)                // window transform
            + (size_t)2 * N * sizeof(float)                   // windows
            + (size_t)FFT_WARPS * 2 * sizeof(double);         // reductions
 }
 
+// Spectra of one (frame, subfield): the tile times the window is transformed
+// row by row (two real rows per complex transform), the windowed mean mu is
+// read off the row transforms' DC terms, mu * window is removed through the
+// window's own transform, and the K+1 non-negative columns are transformed.
 template <int N, typename TIn, int PREC>
 __global__ void __launch_bounds__(FFT_THREADS, 1)
 k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __restrict__ spec,
           float* __restrict__ flux, float* __restrict__ mu) {
+    using GP = Grp<N>;
+    constexpr int P = GP::P, Q = GP::Q, G = GP::G, NG = GP::NG, TB = GP::TB;
     extern __shared__ __align__(16) unsigned char smem[];
     const int K1 = p.K + 1, CP = N + 1;
     float2* C = reinterpret_cast<float2*>(smem);
     float2* scratch = C + (size_t)K1 * CP;
-    float2* stw = scratch + FFT_WARPS * 2 * N;
-    float* swx = reinterpret_cast<float*>(stw + N);
+    float2* stw = scratch + scratch_elems<N>();
+    float2* swf = stw + N;
+    float* swx = reinterpret_cast<float*>(swf + K1);
     float* swy = swx + N;
     double* red = reinterpret_cast<double*>(swy + N);
 
     const int f = blockIdx.x, sl = blockIdx.y, s = sub0 + sl;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = tid / G, g = tid - grp * G;
+    float2* T = scratch + grp * TB;
     const int4 sb = p.subs[s];
     const int x0 = sb.x, y0 = sb.y, w = sb.z, h = sb.w;
     for (int i = tid; i < N; i += FFT_THREADS) {
@@ -90,16 +192,50 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
         swx[i] = p.winx[(size_t)s * N + i];
         swy[i] = p.winy[(size_t)s * N + i];
     }
+    for (int i = tid; i < K1; i += FFT_THREADS) swf[i] = p.winft[(size_t)s * K1 + i];
     __syncthreads();
 
-    const TIn* fr = frames + (size_t)f * p.H * p.W;
-    // pass 1: windowed mean of the tile
-    float acc = 0.f;
-    for (int e = tid; e < w * h; e += FFT_THREADS) {
-        const int y = e / w, x = e - y * w;
-        acc += swx[x] * swy[y] * load_sample(fr + (size_t)(y0 + y) * p.W + x0 + x);
+    const TIn* fr = frames + (size_t)f * p.H * p.W + (size_t)y0 * p.W + x0;
+    // row transforms: group grp of round r handles rows 2(r NG + grp), +1
+    float raw[2][Q];
+    auto fetch = [&](int pr) {
+        const int y1 = 2 * pr, y2 = y1 + 1;
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) {
+            const int x = g + P * n2;
+            const bool inx = g < P && x < w;
+            raw[0][n2] = inx && y1 < h ? load_sample(fr + (size_t)y1 * p.W + x) : 0.f;
+            raw[1][n2] = inx && y2 < h ? load_sample(fr + (size_t)y2 * p.W + x) : 0.f;
+        }
+    };
+    fetch(grp);
+    for (int pr0 = 0; pr0 < N / 2; pr0 += NG) {
+        const int pr = pr0 + grp, y1 = 2 * pr, y2 = y1 + 1;
+        float2 v[Q], X[P];
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) {
+            const float wx = swx[(g + P * n2) & (N - 1)];
+            v[n2] = make_float2(wx * swy[y1] * raw[0][n2], wx * swy[y2] * raw[1][n2]);
+        }
+        if (pr0 + NG < N / 2) fetch(pr + NG);
+        four_step<N, false>(v, X, T, stw, g);
+        if (g < Q) {
+#pragma unroll
+            for (int k1 = 0; k1 < P; ++k1) T[g + Q * k1] = X[k1];
+        }
+        __syncwarp();
+        for (int kx = g; kx < K1; kx += G) {
+            const float2 za = T[kx], zb = T[(N - kx) & (N - 1)];
+            C[kx * CP + y1] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+            C[kx * CP + y2] = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+        }
+        __syncwarp();
     }
-    double dacc = acc;
+    __syncthreads();
+
+    // windowed mean from the DC terms of the row transforms
+    double dacc = 0.0;
+    for (int y = tid; y < N; y += FFT_THREADS) dacc += (double)C[y].x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
     if (lane == 0) red[warp] = dacc;
@@ -108,53 +244,33 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
     for (int i = 0; i < FFT_WARPS; ++i) tot += red[i];
     const double wsum = p.winsum[s];
     const float mean = (float)(tot / wsum);
+    // remove mean * window: row transform of w_x(x) w_y(y) mu is mu w_y(y) Wx(kx)
+    for (int e = tid; e < K1 * h; e += FFT_THREADS) {
+        const int kx = e / h, y = e - kx * h;
+        const float a = mean * swy[y];
+        float2& c = C[kx * CP + y];
+        c.x -= a * swf[kx].x;
+        c.y -= a * swf[kx].y;
+    }
+    __syncthreads();
 
-    // pass 2: row FFTs, two real rows per complex FFT, keep kx = 0..K
-    float2* fa = scratch + warp * 2 * N;
-    float2* fb = fa + N;
-    for (int pr = warp; pr < N / 2; pr += FFT_WARPS) {
-        const int y1 = 2 * pr, y2 = y1 + 1;
-        if (y1 >= h) {
-            for (int kx = lane; kx < K1; kx += 32) {
-                C[kx * CP + y1] = make_float2(0.f, 0.f);
-                C[kx * CP + y2] = make_float2(0.f, 0.f);
-            }
-            continue;
-        }
-        const bool has2 = y2 < h;
-        const TIn* r1 = fr + (size_t)(y0 + y1) * p.W + x0;
-        const TIn* r2 = fr + (size_t)(y0 + (has2 ? y2 : y1)) * p.W + x0;
-        for (int x = lane; x < N; x += 32) {
-            float v1 = 0.f, v2 = 0.f;
-            if (x < w) {
-                v1 = swx[x] * swy[y1] * (load_sample(r1 + x) - mean);
-                if (has2) v2 = swx[x] * swy[y2] * (load_sample(r2 + x) - mean);
-            }
-            fa[x] = make_float2(v1, v2);
-        }
-        __syncwarp();
-        const float2* Z = warp_fft<N, false>(fa, fb, stw, lane);
-        for (int kx = lane; kx < K1; kx += 32) {
-            const float2 za = Z[kx], zb = Z[(N - kx) & (N - 1)];
-            C[kx * CP + y1] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-            C[kx * CP + y2] = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+    // column transforms of kx = 0..K (groups past K transform column K and drop it)
+    for (int c0 = 0; c0 < K1; c0 += NG) {
+        const int kx = c0 + grp;
+        const int kc = kx < K1 ? kx : K1 - 1;
+        float2 v[Q], X[P];
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) v[n2] = g < P ? C[kc * CP + g + P * n2] : make_float2(0.f, 0.f);
+        four_step<N, false>(v, X, T, stw, g);
+        if (kx < K1 && g < Q) {
+#pragma unroll
+            for (int k1 = 0; k1 < P; ++k1) C[kx * CP + g + Q * k1] = X[k1];
         }
         __syncwarp();
     }
     __syncthreads();
 
-    // pass 3: column FFTs of kx = 0..K
-    for (int kx = warp; kx < K1; kx += FFT_WARPS) {
-        float2* col = C + (size_t)kx * CP;
-        for (int y = lane; y < N; y += 32) fa[y] = col[y];
-        __syncwarp();
-        const float2* Z = warp_fft<N, false>(fa, fb, stw, lane);
-        for (int y = lane; y < N; y += 32) col[y] = Z[y];
-        __syncwarp();
-    }
-    __syncthreads();
-
-    // pass 4: normalise by the windowed flux and store the box ky = -R..K
+    // normalise by the windowed flux and store the box ky = -R..K
     const double fl = (double)mean * wsum;
     const float inv = (float)(1.0 / fl);
     const size_t base = ((size_t)sl * F + f) * p.box_rows * p.box_pitch;
@@ -190,8 +306,8 @@ k_inverse(PlanDev p, int F, int sub0, const float* __restrict__ A, const double2
     const int K = p.K, K1 = K + 1, CP = N + 1;
     float2* C = reinterpret_cast<float2*>(smem);
     float2* scratch = C + (size_t)K1 * CP;
-    float2* stw = scratch + FFT_WARPS * 2 * N;
-    float* swx = reinterpret_cast<float*>(stw + N);
+    float2* stw = scratch + scratch_elems<N>();
+    float* swx = reinterpret_cast<float*>(stw + N + K1);
     float* swy = swx + N;
     double* red = reinterpret_cast<double*>(swy + N);
 

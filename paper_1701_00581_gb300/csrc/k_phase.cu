@@ -7,8 +7,9 @@
 // ascending order (points of one ring never depend on each other).  The
 // ring's work is a list of (point, bispectrum tile) items; the 16 warps
 // take items round-robin, four at a time so that their B loads are in
-// flight together, and sum exp(i(phi(w-v) + phi(v))) conj B over the 64
-// offsets of the tile (FP32 products, FP64 sums) into one partial per item.
+// flight together, and sum exp(i(phi(w-v) + phi(v))) conj B over the
+// offsets of the tile (FP32 products and item sums; GB300's FP64 rate is a
+// small fraction of its FP32 rate) into one partial per item.
 // Then one thread per point adds its partials in a fixed order and stores
 // z(w) = S / |S|: the result does not depend on scheduling.  The known
 // phasors live in shared memory (FP32 copy for the products); the FP64
@@ -40,7 +41,7 @@ __device__ __forceinline__ float2 zget(const float2* zs, int pitch, int K, int k
 
 constexpr int PH_UNROLL = 4;          // items in flight per warp
 
-__global__ void __launch_bounds__(PH_THREADS, 1)
+__global__ void __launch_bounds__(PH_THREADS, 2)
 k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         double2* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -74,47 +75,60 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
     const int R2 = p.R * p.R;
     const bool unit = p.weight == SM_W_UNIT;
     const float2* Bs = B + (size_t)sl * p.n_tiles * TILE_PAIRS;
+    constexpr int NH = TILE_V / 32;        // offsets per lane per item
+    // one batch = up to PH_UNROLL items of a warp; B does not depend on the
+    // phases, so the next ring's first batch is loaded before the barriers
+    float2 bv[PH_UNROLL][NH];
+    int wx[PH_UNROLL], wy[PH_UNROLL], tx0[PH_UNROLL], ty0[PH_UNROLL];
+    unsigned okm[PH_UNROLL];
+    auto load_batch = [&](int base, int i1) {
+#pragma unroll
+        for (int q = 0; q < PH_UNROLL; ++q) {
+            const int it = base + q * PH_WARPS;
+            okm[q] = 0;
+#pragma unroll
+            for (int h = 0; h < NH; ++h) bv[q][h] = make_float2(0.f, 0.f);
+            if (it < i1) {
+                const int2 item = p.items[it];
+                const int2 w = p.points[item.x];
+                const int4 T = p.tiles[item.y];
+                wx[q] = w.x;
+                wy[q] = w.y;
+                tx0[q] = T.z;
+                ty0[q] = T.w;
+                const int wxl = (w.x + K) % smi::WBX, wyl = w.y % smi::WBY;
+                const float2* bp = Bs + (size_t)item.y * TILE_PAIRS + (wyl * smi::WBX + wxl) * TILE_V;
+#pragma unroll
+                for (int h = 0; h < NH; ++h) {
+                    const int vl = lane + 32 * h;
+                    if (pair_used(w.x, w.y, T.z + (vl % smi::VBX), T.w + (vl / smi::VBX), p.r2i, R2)) {
+                        okm[q] |= 1u << h;
+                        bv[q][h] = bp[vl];
+                    }
+                }
+            }
+        }
+    };
+    load_batch(p.ring_items[0] + warp, p.ring_items[1]);
     for (int r = 0; r < p.n_rings; ++r) {
         const int i0 = p.ring_items[r], i1 = p.ring_items[r + 1];
         // (1) every (point, tile) item of the ring: warp-summed phasor terms
         for (int base = i0 + warp; base < i1; base += PH_WARPS * PH_UNROLL) {
-            float2 bv[PH_UNROLL][2];
-            int2 wq[PH_UNROLL];
-            int4 tq[PH_UNROLL];
-            bool ok[PH_UNROLL][2];
-#pragma unroll
-            for (int q = 0; q < PH_UNROLL; ++q) {
-                const int it = base + q * PH_WARPS;
-                ok[q][0] = ok[q][1] = false;
-                bv[q][0] = bv[q][1] = make_float2(0.f, 0.f);
-                if (it < i1) {
-                    const int2 item = p.items[it];
-                    const int2 w = p.points[item.x];
-                    const int4 T = p.tiles[item.y];
-                    wq[q] = w;
-                    tq[q] = T;
-                    const int wxl = (w.x + K) % smi::WBX, wyl = w.y % smi::WBY;
-                    const float2* bp = Bs + (size_t)item.y * TILE_PAIRS + (wyl * smi::WBX + wxl) * TILE_V;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int vl = lane + 32 * h;
-                        ok[q][h] = pair_used(w.x, w.y, T.z + (vl % smi::VBX), T.w + (vl / smi::VBX), p.r2i, R2);
-                        if (ok[q][h]) bv[q][h] = bp[vl];
-                    }
-                }
-            }
+            if (base != i0 + warp) load_batch(base, i1);
 #pragma unroll
             for (int q = 0; q < PH_UNROLL; ++q) {
                 const int it = base + q * PH_WARPS;
                 if (it >= i1) break;                       // warp-uniform
-                double sx = 0.0, sy = 0.0;
+                // FP32 products and per-item sums (at most 64 terms); the
+                // per-point sum and the phasor state are FP64
+                float sx = 0.f, sy = 0.f;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (!ok[q][h]) continue;
+                for (int h = 0; h < NH; ++h) {
+                    if (!(okm[q] & (1u << h))) continue;
                     const int vl = lane + 32 * h;
-                    const int vx = tq[q].z + (vl % smi::VBX), vy = tq[q].w + (vl / smi::VBX);
+                    const int vx = tx0[q] + (vl % smi::VBX), vy = ty0[q] + (vl / smi::VBX);
                     const float2 b = bv[q][h];
-                    const float2 zu = zget(zs, pitch, K, wq[q].x - vx, wq[q].y - vy);
+                    const float2 zu = zget(zs, pitch, K, wx[q] - vx, wy[q] - vy);
                     const float2 zv = zget(zs, pitch, K, vx, vy);
                     const float2 c = make_float2(zu.x * zv.x - zu.y * zv.y, zu.x * zv.y + zu.y * zv.x);
                     float tx = c.x * b.x + c.y * b.y;      // c * conj(b)
@@ -136,9 +150,10 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
                     sx += __shfl_xor_sync(0xffffffffu, sx, o);
                     sy += __shfl_xor_sync(0xffffffffu, sy, o);
                 }
-                if (lane == 0) part[it - i0] = make_double2(sx, sy);
+                if (lane == 0) part[it - i0] = make_double2((double)sx, (double)sy);
             }
         }
+        if (r + 1 < p.n_rings) load_batch(i1 + warp, p.ring_items[r + 2]);
         __syncthreads();
         // (2) one thread per point: sum its items in order, normalise
         const int pe = p.ring_start[r + 1];

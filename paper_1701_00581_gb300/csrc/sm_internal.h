@@ -14,12 +14,13 @@ namespace smi {
 // block of WBX x WBY target frequencies w and a block of VBX x VBY offsets v.
 // Warp q of the CTA owns offset row vy0 + q; lane (wyl, gx) owns the four
 // targets (wx0 + 4 gx + j, wy0 + wyl), j = 0..3, and the eight offsets
-// (vx0 + kk, vy0 + q), kk = 0..7.
-constexpr int WBX = 16, WBY = 8, VBX = 8, VBY = 8;
+// (vx0 + kk, vy0 + q), kk = 0..7.  Four warps per CTA let four CTAs share
+// an SM, so warps of different tiles fill each other's idle issue slots.
+constexpr int WBX = 16, WBY = 8, VBX = 8, VBY = 4;
 constexpr int TILE_W = WBX * WBY;            // 128 targets
-constexpr int TILE_V = VBX * VBY;            // 64 offsets
-constexpr int TILE_PAIRS = TILE_W * TILE_V;  // 8192 (w, v) slots
-constexpr int BISPEC_THREADS = 256;
+constexpr int TILE_V = VBX * VBY;            // 32 offsets
+constexpr int TILE_PAIRS = TILE_W * TILE_V;  // 4096 (w, v) slots
+constexpr int BISPEC_THREADS = 32 * VBY;     // one warp per offset row
 
 constexpr float FP16_SCALE = 16384.0f;       // |I_n| <= 1 -> fits half with margin
 constexpr float FP16_INV_SCALE = 1.0f / 16384.0f;
@@ -38,6 +39,7 @@ struct PlanDev {
     const float* winx;       // [n_sub][N] window along x (0 beyond the extent)
     const float* winy;       // [n_sub][N]
     const double* winsum;    // [n_sub] sum of the 2-D window
+    const float2* winft;     // [n_sub][K+1] DFT of the x window at kx = 0..K
     const float2* tw;        // [N] exp(-2 pi i k / N)
     const int4* tiles;       // [n_tiles] wx0, wy0, vx0, vy0
     const int* ring_start;   // [n_rings + 1]

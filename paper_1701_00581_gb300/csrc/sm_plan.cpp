@@ -117,6 +117,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     pl->subs.resize(d.n_sub);
     std::vector<float> winx((size_t)d.n_sub * N, 0.f), winy((size_t)d.n_sub * N, 0.f);
     std::vector<double> winsum(d.n_sub);
+    std::vector<float2> winft((size_t)d.n_sub * (K + 1));
     for (int j = 0; j < d.nsy; ++j)
         for (int i = 0; i < d.nsx; ++i) {
             const int s = j * d.nsx + i;
@@ -126,6 +127,15 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
             for (int x = 0; x < w; ++x) { double v = tukey_at(x, w, ch->taper); winx[(size_t)s * N + x] = (float)v; sx += v; }
             for (int y = 0; y < h; ++y) { double v = tukey_at(y, h, ch->taper); winy[(size_t)s * N + y] = (float)v; sy += v; }
             winsum[s] = sx * sy;
+            for (int kx = 0; kx <= K; ++kx) {
+                double re = 0, im = 0;
+                for (int x = 0; x < w; ++x) {
+                    const double v = tukey_at(x, w, ch->taper), a = -2.0 * M_PI * kx * x / N;
+                    re += v * std::cos(a);
+                    im += v * std::sin(a);
+                }
+                winft[(size_t)s * (K + 1) + kx] = make_float2((float)re, (float)im);
+            }
         }
 
     // twiddles exp(-2 pi i k / N)
@@ -268,6 +278,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         {pl->items.data(), pl->items.size() * sizeof(int2), 0},
         {pl->ring_items.data(), pl->ring_items.size() * sizeof(int), 0},
         {pl->point_items.data(), pl->point_items.size() * sizeof(int), 0},
+        {winft.data(), winft.size() * sizeof(float2), 0},
     };
     size_t total = 0;
     for (auto& p : pcs) { p.off = total; total += align256(std::max<size_t>(p.bytes, 1)); }
@@ -295,6 +306,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.items = (const int2*)at(11);
     d.ring_items = (const int*)at(12);
     d.point_items = (const int*)at(13);
+    d.winft = (const float2*)at(14);
     *out = pl;
     return SM_OK;
 }
@@ -359,18 +371,30 @@ extern "C" int sm_model_stf(const sm_channel* ch, int F, const double* d_over_r0
         if (!(d_over_r0[i] > 0.0)) { set_error("d_over_r0 must be > 0"); return SM_EINVAL; }
     const int N = ch->N;
     const double r = ch->fc * N;
+    // The model depends on |k| only and vanishes with T0 outside the cutoff
+    // disk, so it is evaluated once per distinct |k|^2 inside the disk.
+    std::vector<double> a(F), b(F);
+    for (int f = 0; f < F; ++f) {
+        a[f] = 6.88 * std::pow(d_over_r0[f], 5.0 / 3.0);
+        b[f] = ch->ck / (d_over_r0[f] * d_over_r0[f]);
+    }
+    const int qmax = (N / 2) * (N / 2) * 2;
+    std::vector<double> byq(qmax + 1, -1.0);
     std::vector<double> acc((size_t)N * N, 0.0);
     for (int iy = 0; iy < N; ++iy)
         for (int ix = 0; ix < N; ++ix) {
-            const double ky = iy - N / 2, kx = ix - N / 2;
-            const double rho = std::sqrt(kx * kx + ky * ky) / r;
-            const double t0 = rho <= 1.0 ? (2.0 / M_PI) * (std::acos(rho) - rho * std::sqrt(1.0 - rho * rho)) : 0.0;
-            double s = 0.0;
-            for (int f = 0; f < F; ++f) {
-                const double d = d_over_r0[f];
-                s += t0 * t0 * std::exp(-6.88 * std::pow(rho * d, 5.0 / 3.0)) + ch->ck * t0 / (d * d);
+            const int ky = iy - N / 2, kx = ix - N / 2, q = kx * kx + ky * ky;
+            if (byq[q] < 0.0) {
+                const double rho = std::sqrt((double)q) / r;
+                double s = 0.0;
+                if (rho <= 1.0) {
+                    const double t0 = (2.0 / M_PI) * (std::acos(rho) - rho * std::sqrt(1.0 - rho * rho));
+                    const double t = std::pow(rho, 5.0 / 3.0);
+                    for (int f = 0; f < F; ++f) s += t0 * t0 * std::exp(-a[f] * t) + b[f] * t0;
+                }
+                byq[q] = s / F;
             }
-            acc[(size_t)iy * N + ix] = s / F;
+            acc[(size_t)iy * N + ix] = byq[q];
         }
     const double c = acc[(size_t)(N / 2) * N + N / 2];
     for (size_t i = 0; i < acc.size(); ++i) stf[i] = acc[i] / c;

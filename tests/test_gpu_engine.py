@@ -1,0 +1,149 @@
+"""Serving engine (sm_open / sm_submit_burst / sm_poll / sm_close) on the GPU.
+
+A burst served by the engine gives the same mosaic as the plain stage path,
+and the same mosaic alone as in a mix of concurrently admitted bursts; the
+admission and error paths return their status codes without faulting.
+"""
+import numpy as np
+import pytest
+
+from synth import burst as S
+
+from . import _cases as CS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_00581_gb300 import build
+    build.build()
+    return t
+
+
+def _bursts(n):
+    spec = CS.RAGGED["spec"]
+    return [S.make_burst(spec, channel=11, burst=i) for i in range(n)]
+
+
+def _plain(torch, ch, b):
+    from paper_1701_00581_gb300 import Plan
+    plan = Plan(ch)
+    stf = plan.model_stf(b["d_over_r0"])
+    g = CS.gpu_run(plan, b["frames"], stf)
+    return g["out"], g["valid"]
+
+
+def _serve_one(eng, b, H, W):
+    out = np.zeros((H, W), np.float32)
+    valid = np.zeros((H, W), np.uint8)
+    t = eng.submit(0, b["frames"], out, valid, d_over_r0=b["d_over_r0"])
+    st, res = eng.poll(t, -1)
+    assert st == 0 and res["gpu_ms"] > 0
+    return out, valid.astype(bool)
+
+
+def test_engine_matches_plain_path(torch):
+    from paper_1701_00581_gb300 import Engine
+    ch = CS.gpu_channel("ragged")
+    b = _bursts(1)[0]
+    ref_out, ref_valid = _plain(torch, ch, b)
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2)
+    out, valid = _serve_one(eng, b, 110, 150)
+    eng.close()
+    assert np.array_equal(valid, ref_valid)
+    assert np.array_equal(out, ref_out)
+
+
+def test_alone_equals_in_the_mix(torch):
+    """Bursts admitted while others are on the device give the same mosaic
+    (bitwise) as each burst served alone."""
+    from paper_1701_00581_gb300 import Engine
+    ch = CS.gpu_channel("ragged")
+    bursts = _bursts(4)
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=3)
+    alone = [_serve_one(eng, b, 110, 150) for b in bursts]
+    outs = [np.zeros((110, 150), np.float32) for _ in bursts]
+    pending, k = [], 0
+    while k < len(bursts) or pending:
+        while k < len(bursts):
+            t = eng.try_submit(0, bursts[k]["frames"], outs[k], d_over_r0=bursts[k]["d_over_r0"])
+            if t is None:
+                break
+            pending.append((t, k))
+            k += 1
+        t, i = pending.pop(0)
+        st, _ = eng.poll(t, -1)
+        assert st == 0
+    eng.close()
+    for (o, _), m in zip(alone, outs):
+        assert np.array_equal(o, m)
+
+
+def test_two_channels_in_one_engine(torch):
+    from paper_1701_00581_gb300 import Channel, Engine
+    c0 = CS.gpu_channel("ragged")
+    c1 = Channel(W=96, H=80, N=64, R=6, stride=32, taper=8, max_frames=5)
+    b0 = _bursts(1)[0]
+    b1 = S.make_burst(S.BurstSpec(W=96, H=80, F=5, N=64, dr0=(4.0, 6.0), counts=True), channel=12)
+    eng = Engine([c0, c1], hbm_budget_bytes=1 << 30, max_inflight=2)
+    o0 = np.zeros((110, 150), np.float32)
+    o1 = np.zeros((80, 96), np.float32)
+    t0 = eng.submit(0, b0["frames"], o0, d_over_r0=b0["d_over_r0"])
+    t1 = eng.submit(1, b1["frames"], o1, d_over_r0=b1["d_over_r0"])
+    assert eng.poll(t1, -1)[0] == 0 and eng.poll(t0, -1)[0] == 0
+    eng.close()
+    ref1, _ = _plain(torch, c1, b1)
+    assert np.array_equal(o1, ref1)
+    assert np.isfinite(o0).all()
+
+
+def test_admission_and_error_statuses(torch):
+    from paper_1701_00581_gb300 import Engine, SpeckleError, _lib
+    ch = CS.gpu_channel("ragged")
+    b = _bursts(1)[0]
+    # a budget smaller than one burst: SM_ENOMEM
+    eng = Engine([ch], hbm_budget_bytes=1 << 20, max_inflight=1)
+    with pytest.raises(SpeckleError) as e:
+        eng.submit(0, b["frames"], np.zeros((110, 150), np.float32), d_over_r0=b["d_over_r0"])
+    assert e.value.status == _lib.SM_ENOMEM
+    eng.close()
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=1)
+    out = np.zeros((110, 150), np.float32)
+    t = eng.submit(0, b["frames"], out, d_over_r0=b["d_over_r0"])
+    # the only slot is taken: SM_EBUSY, nothing queued
+    assert eng.try_submit(0, b["frames"], np.zeros_like(out), d_over_r0=b["d_over_r0"]) is None
+    st, _ = eng.poll(t, 0)
+    assert st in (_lib.SM_OK, _lib.SM_PENDING)
+    if st != _lib.SM_OK:
+        assert eng.poll(t, -1)[0] == _lib.SM_OK
+    # a finished ticket is released
+    with pytest.raises(SpeckleError) as e:
+        eng.poll(t, 0)
+    assert e.value.status == _lib.SM_ENOTFOUND
+    # bad arguments
+    with pytest.raises(SpeckleError) as e:
+        eng.submit(5, b["frames"], out, d_over_r0=b["d_over_r0"])
+    assert e.value.status == _lib.SM_EINVAL
+    with pytest.raises(SpeckleError) as e:
+        eng.submit(0, b["frames"], out)      # neither stf nor d_over_r0
+    assert e.value.status == _lib.SM_EINVAL
+    eng.close()
+
+
+def test_close_with_pending_tickets(torch):
+    from paper_1701_00581_gb300 import Engine
+    ch = CS.gpu_channel("ragged")
+    bursts = _bursts(2)
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2)
+    outs = [np.zeros((110, 150), np.float32) for _ in bursts]
+    for b, o in zip(bursts, outs):
+        eng.submit(0, b["frames"], o, d_over_r0=b["d_over_r0"])
+    eng.close()                       # waits for the device, releases everything
+    eng2 = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=1)
+    o, _ = _serve_one(eng2, bursts[0], 110, 150)
+    eng2.close()
+    assert np.isfinite(o).all()
