@@ -183,6 +183,26 @@ int sm_reconstruct(const sm_plan* plan, const void* frames, int frame_type, int 
                    const double* stf, int nsub_chunk, void* ws,
                    const sm_workspace_layout* lay, float* out, uint8_t* valid, void* stream);
 
+/* Allocation-free whole path.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory once they
+ * are running, such as a camera or telescope control loop that fixes all of
+ * its device memory at start-up (an allocation can synchronise the device
+ * and stall frame acquisition), or a plug-in whose host framework owns every
+ * device allocation.  Same arguments and result as sm_reconstruct, but the
+ * workspace is a fixed array of SM_NOALLOC_SCRATCH_BYTES in the library's
+ * own device image (every GPU that loads the library holds it until the
+ * process exits), so the call allocates nothing.  Subfields go through in
+ * the largest chunks that fit; a channel whose workspace does not fit even
+ * one subfield at a time gets SM_ENOMEM (the message states both sizes).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (other streams or threads) race, and the
+ * caller must serialise them.  Nothing in the array has to start at zero:
+ * every value a call reads is written earlier in the same call.            */
+#define SM_NOALLOC_SCRATCH_BYTES (64u << 20)
+int sm_reconstruct_noalloc(const sm_plan* plan, const void* frames, int frame_type, int F,
+                           const double* stf, float* out, uint8_t* valid, void* stream);
+
 /* Model STF (Sect. 3.2, calibrated by r0): per frame
  * T0^2 exp(-6.88 (rho D/r0)^(5/3)) + ck (r0/D)^2 T0, averaged over the F
  * frames' D/r0 and normalised to 1 at k = 0.  Host only; stf_out is host

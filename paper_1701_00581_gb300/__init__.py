@@ -181,6 +181,17 @@ class Plan:
         check(self.lib.sm_reconstruct(self.h, _ptr(frames), ft, F, _ptr(stf), chunk, _ptr(ws), C.byref(lay),
                                       _ptr(out), _ptr(valid), _stream(stream)), "sm_reconstruct")
 
+    def reconstruct_noalloc(self, frames, F, stf, out, valid=None, stream=None):
+        """sm_reconstruct_noalloc: the whole path on the library's fixed scratch array,
+        for callers that may not allocate device memory while running."""
+        check(self.lib.sm_reconstruct_noalloc(self.h, _ptr(frames), _frame_type(frames), F, _ptr(stf),
+                                              _ptr(out), _ptr(valid), _stream(stream)),
+              "sm_reconstruct_noalloc")
+
+
+def _frame_type(frames) -> int:
+    return SM_U16 if str(frames.dtype).endswith("uint16") else SM_F32
+
 
 class Engine:
     """sm_open / sm_submit_burst / sm_poll / sm_close (the serving engine)."""

@@ -75,6 +75,7 @@ SIGNATURES = {
     "sm_stage_inverse": (_I, [_P, _I, _I, _I, _P, _LAY, _P]),
     "sm_stage_mosaic": (_I, [_P, _P, _LAY, _P, _P, _P]),
     "sm_reconstruct": (_I, [_P, _P, _I, _I, _P, _I, _P, _LAY, _P, _P, _P]),
+    "sm_reconstruct_noalloc": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
     "sm_model_stf": (_I, [C.POINTER(sm_channel), _I, _P, _P]),
     "sm_open": (_I, [C.POINTER(sm_config), C.POINTER(_P)]),
     "sm_submit_burst": (_I, [_P, C.POINTER(sm_burst), C.POINTER(C.c_uint64)]),
