@@ -39,7 +39,7 @@ __device__ __forceinline__ float2 zget(const float2* zs, int pitch, int K, int k
     return make_float2(t.x, -t.y);
 }
 
-constexpr int PH_UNROLL = 4;          // items in flight per warp
+constexpr int PH_UNROLL = 8;          // items in flight per warp
 
 __global__ void __launch_bounds__(PH_THREADS, 2)
 k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
@@ -77,34 +77,32 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
     const float2* Bs = B + (size_t)sl * p.n_tiles * TILE_PAIRS;
     constexpr int NH = TILE_V / 32;        // offsets per lane per item
     // one batch = up to PH_UNROLL items of a warp; B does not depend on the
-    // phases, so the next ring's first batch is loaded before the barriers
-    float2 bv[PH_UNROLL][NH];
-    int wx[PH_UNROLL], wy[PH_UNROLL], tx0[PH_UNROLL], ty0[PH_UNROLL];
-    unsigned okm[PH_UNROLL];
+    // phases, so the next ring's first batch is loaded before the barriers.
+    // Per item: w and the tile's offset origin packed as four signed bytes
+    // (the plan keeps |coordinates| < 128), the B value of this lane's offset, and a
+    // bit saying whether that (w, v) pair is read.
+    static_assert(NH == 1, "one offset per lane per item");
+    float2 bv[PH_UNROLL];
+    unsigned pk[PH_UNROLL];
+    unsigned okm = 0;
     auto load_batch = [&](int base, int i1) {
+        okm = 0;
 #pragma unroll
         for (int q = 0; q < PH_UNROLL; ++q) {
             const int it = base + q * PH_WARPS;
-            okm[q] = 0;
-#pragma unroll
-            for (int h = 0; h < NH; ++h) bv[q][h] = make_float2(0.f, 0.f);
+            bv[q] = make_float2(0.f, 0.f);
+            pk[q] = 0;
             if (it < i1) {
                 const int2 item = p.items[it];
                 const int2 w = p.points[item.x];
                 const int4 T = p.tiles[item.y];
-                wx[q] = w.x;
-                wy[q] = w.y;
-                tx0[q] = T.z;
-                ty0[q] = T.w;
+                pk[q] = (unsigned)(w.x & 255) | ((unsigned)(w.y & 255) << 8) |
+                        ((unsigned)(T.z & 255) << 16) | ((unsigned)(T.w & 255) << 24);
                 const int wxl = (w.x + K) % smi::WBX, wyl = w.y % smi::WBY;
                 const float2* bp = Bs + (size_t)item.y * TILE_PAIRS + (wyl * smi::WBX + wxl) * TILE_V;
-#pragma unroll
-                for (int h = 0; h < NH; ++h) {
-                    const int vl = lane + 32 * h;
-                    if (pair_used(w.x, w.y, T.z + (vl % smi::VBX), T.w + (vl / smi::VBX), p.r2i, R2)) {
-                        okm[q] |= 1u << h;
-                        bv[q][h] = bp[vl];
-                    }
+                if (pair_used(w.x, w.y, T.z + (lane % smi::VBX), T.w + (lane / smi::VBX), p.r2i, R2)) {
+                    okm |= 1u << q;
+                    bv[q] = bp[lane];
                 }
             }
         }
@@ -119,16 +117,15 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
             for (int q = 0; q < PH_UNROLL; ++q) {
                 const int it = base + q * PH_WARPS;
                 if (it >= i1) break;                       // warp-uniform
-                // FP32 products and per-item sums (at most 64 terms); the
+                // FP32 products and per-item sums (one term per lane); the
                 // per-point sum and the phasor state are FP64
                 float sx = 0.f, sy = 0.f;
-#pragma unroll
-                for (int h = 0; h < NH; ++h) {
-                    if (!(okm[q] & (1u << h))) continue;
-                    const int vl = lane + 32 * h;
-                    const int vx = tx0[q] + (vl % smi::VBX), vy = ty0[q] + (vl / smi::VBX);
-                    const float2 b = bv[q][h];
-                    const float2 zu = zget(zs, pitch, K, wx[q] - vx, wy[q] - vy);
+                if (okm & (1u << q)) {
+                    const int wx = (signed char)(pk[q] & 255), wy = (signed char)((pk[q] >> 8) & 255);
+                    const int vx = (signed char)((pk[q] >> 16) & 255) + (lane % smi::VBX);
+                    const int vy = (signed char)((pk[q] >> 24) & 255) + (lane / smi::VBX);
+                    const float2 b = bv[q];
+                    const float2 zu = zget(zs, pitch, K, wx - vx, wy - vy);
                     const float2 zv = zget(zs, pitch, K, vx, vy);
                     const float2 c = make_float2(zu.x * zv.x - zu.y * zv.y, zu.x * zv.y + zu.y * zv.x);
                     float tx = c.x * b.x + c.y * b.y;      // c * conj(b)
@@ -142,8 +139,8 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
                             tx = ty = 0.f;
                         }
                     }
-                    sx += tx;
-                    sy += ty;
+                    sx = tx;
+                    sy = ty;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {

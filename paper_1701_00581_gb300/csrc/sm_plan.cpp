@@ -59,6 +59,7 @@ int validate_channel(const sm_channel* ch) {
     const int K = (int)std::floor(r);
     if (K < 2) { set_error("cutoff radius fc*N must be >= 2"); return SM_EINVAL; }
     if (ch->R < 1 || ch->R > K) { set_error("R must be in 1..floor(fc*N)"); return SM_EINVAL; }
+    if (ch->R + VBX > 127) { set_error("R must be below 120 (offset tiles use byte coordinates)"); return SM_EINVAL; }
     if (ch->taper < 0 || ch->taper > ch->N / 4) { set_error("taper must be in 0..N/4"); return SM_EINVAL; }
     if (ch->spectra_prec < SM_FP32 || ch->spectra_prec > SM_BF16) {
         set_error("spectra_prec must be SM_FP32, SM_FP16 or SM_BF16"); return SM_EINVAL;
