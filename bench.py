@@ -165,6 +165,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- ncu traffic
+def kernel_traffic(kernel_file: str, units_per_launch: float):
+    """DRAM bytes (read + write) per launch of the dominant kernel from the
+    committed ncu summary, scaled from the captured case to this launch by
+    the units processed; None when the kernel source changed since the
+    counters were taken (the summary records the source's SHA-256)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_bispectrum_traffic.json")
+    src = os.path.join(ROOT, "paper_1701_00581_gb300", "csrc", kernel_file)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    rec = json.load(open(path))
+    if rec.get("source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+        return None
+    return rec["dram_bytes_per_unit"] * units_per_launch
+
+
 # ---------------------------------------------------------------------------- ranks
 def max_over_ranks(x: float, device=None) -> float:
     """Largest value of x over all ranks (x itself when not distributed)."""
@@ -271,8 +288,10 @@ def main():
     if os.path.exists(peaks_path):
         sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max))
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    traffic = kernel_traffic("k_bispec.cu", n_sub)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                "traffic": None if traffic is None else int(traffic),
                 "kernel": "k_bispectrum", "kernel_ms": round(bisp_ms, 3),
                 "note": (f"{FLOPS_PER_TRIPLE} flops x {triples:.3e} used triples per launch; peak = "
                          f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "

@@ -12,10 +12,10 @@
 // the whole burst.  Per frame the CTA stages three rectangles of the frame
 // spectrum in shared memory: the targets W (8 x 16), the offsets V (4 x 8)
 // and U = W - V (11 x 23).  For its 32 pairs a thread reads 4 values of W,
-// 8 broadcast values of V and an 11-wide sliding window of U, so each
-// triple product costs 8 FP32 FMA-pipe instructions and ~0.7 shared loads.
-// The next frame's rectangles are prefetched into registers while the
-// current frame is multiplied out.  A warp skips the offset columns (and so
+// 8 broadcast values of V and an 11-wide sliding window of U (12 shared
+// loads of 16 bytes for 32 pairs), so each triple product costs 8 FP32
+// FMA-pipe instructions.  FP32 spectra are staged by cp.async, four frames
+// per barrier, while the previous four frames are multiplied out.  A warp skips the offset columns (and so
 // whole tiles) in which none of its lanes owns a used pair.  Accumulators are
 // written once per burst.
 #include "sm_internal.h"
@@ -27,21 +27,24 @@ using smi::TILE_PAIRS;
 using smi::TILE_V;
 using smi::TILE_W;
 
-constexpr int PW = 17;                  // row pitch of W in smem (conflict-free, see below)
-constexpr int PU = 25;                  // row pitch of U in smem
-constexpr int UR = smi::WBY + smi::VBY - 1;     // 15 rows of U
+constexpr int PW = 18;                  // row pitch of W in smem (float2)
+constexpr int PU = 26;                  // row pitch of U in smem (float2)
+constexpr int UR = smi::WBY + smi::VBY - 1;     // 11 rows of U
 constexpr int UC = smi::WBX + smi::VBX - 1;     // 23 cols of U
 constexpr int OFF_W = 0;
-constexpr int OFF_V = smi::WBY * PW;                      // 136
-constexpr int OFF_U = OFF_V + smi::VBY * smi::VBX;        // 168
-constexpr int BUF = OFF_U + UR * PU;                      // 443 float2 per frame buffer
+constexpr int OFF_V = smi::WBY * PW;                      // 144
+constexpr int OFF_U = OFF_V + smi::VBY * smi::VBX;        // 176
+constexpr int BUF = OFF_U + UR * PU;                      // 462 float2 per frame buffer
 constexpr int NLOAD = smi::WBY * smi::WBX + smi::VBY * smi::VBX + UR * UC;  // 413
 constexpr int THREADS = smi::BISPEC_THREADS;
 constexpr int LPT = (NLOAD + THREADS - 1) / THREADS;      // 4 elements per thread
+static_assert(OFF_V % 2 == 0 && OFF_U % 2 == 0 && BUF % 2 == 0 && PW % 2 == 0 && PU % 2 == 0,
+              "16-byte shared loads need even float2 offsets");
 
-// Bank check (64-bit accesses, half-warp phases): lanes 0..15 hold
-// wyl = 0..3, gx = 0..3 and read element wyl*P + 4*gx + m; with P = 17 or
-// 25 the 16 word-pairs 2*(wyl*P + 4*gx) mod 32 are all distinct.
+// Bank check (16-byte loads, 8-lane phases): lanes 0..7 hold wyl = 0, 1 and
+// gx = 0..3.  Targets: 16-byte slot 9 wyl + 2 gx (+ j/2) -> {0,2,4,6} + {0,1}
+// mod 8, distinct.  Differences: slot 13 row + 2 gx + q, rows of lanes 0..7
+// differ by 1 -> {0,2,4,6} + {0,5} mod 8, distinct.  Offsets: broadcast.
 
 template <int PREC>
 __device__ __forceinline__ float2 load_spec(const void* spec, size_t idx) {
@@ -64,10 +67,63 @@ __device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2
     return inH && w2 >= 2 && w2 <= r2i && v2 > 0 && v2 <= R2 && v2 < w2 && u2 < w2;
 }
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(sa), "l"(gmem), "r"(bytes));
+}
+
+// One frame of the thread's 4 x 8 pairs from the staged rectangles.
+__device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, int wyl, int gx, int warp,
+                                                 unsigned kkmask, float2 (&acc)[4][smi::VBX]) {
+    const float4* w4 = reinterpret_cast<const float4*>(Sb + OFF_W + wyl * PW + 4 * gx);
+    const float4 w01 = w4[0], w23 = w4[1];
+    const float2 a[4] = {make_float2(w01.x, -w01.y), make_float2(w01.z, -w01.w),   // conj I(w)
+                         make_float2(w23.x, -w23.y), make_float2(w23.z, -w23.w)};
+    const float4* u4 = reinterpret_cast<const float4*>(Sb + OFF_U + (wyl - warp + smi::VBY - 1) * PU + 4 * gx);
+    float2 c[12];                                    // I(w - v), m = j - kk + 7
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float4 t = u4[q];
+        c[2 * q] = make_float2(t.x, t.y);
+        c[2 * q + 1] = make_float2(t.z, t.w);
+    }
+    const float4* v4 = reinterpret_cast<const float4*>(Sb + OFF_V + warp * smi::VBX);
+#pragma unroll
+    for (int k2 = 0; k2 < smi::VBX / 2; ++k2) {
+        if (!(kkmask & (3u << (2 * k2)))) continue;   // warp-uniform
+        const float4 bb = v4[k2];                       // I(v) for kk = 2 k2, 2 k2 + 1 (broadcast)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int kk = 2 * k2 + e;
+            if (!(kkmask & (1u << kk))) continue;       // warp-uniform
+            const float2 b = e == 0 ? make_float2(bb.x, bb.y) : make_float2(bb.z, bb.w);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 u = c[j - kk + 7];
+                const float px = fmaf(u.x, b.x, -u.y * b.y);
+                const float py = fmaf(u.x, b.y, u.y * b.x);
+                acc[j][kk].x = fmaf(px, a[j].x, fmaf(-py, a[j].y, acc[j][kk].x));
+                acc[j][kk].y = fmaf(px, a[j].y, fmaf(py, a[j].x, acc[j][kk].y));
+            }
+        }
+    }
+}
+
+// Staging: FP32 spectra go straight from global to shared memory by cp.async
+// (zero-filled outside the box), FB frames per stage in a two-stage ring, so
+// one barrier serves FB frames; half-precision spectra are converted in
+// registers one frame ahead.
+template <int PREC> struct Staging;
+template <> struct Staging<SM_FP32> { static constexpr bool ASYNC = true;  static constexpr int FB = 4; };
+template <> struct Staging<SM_FP16> { static constexpr bool ASYNC = false; static constexpr int FB = 1; };
+template <> struct Staging<SM_BF16> { static constexpr bool ASYNC = false; static constexpr int FB = 1; };
+
 template <int PREC>
 __global__ void __launch_bounds__(THREADS, 4)
 k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict__ B) {
-    __shared__ __align__(16) float2 S[2 * BUF];
+    constexpr bool ASYNC = Staging<PREC>::ASYNC;
+    constexpr int FB = Staging<PREC>::FB;
+    __shared__ __align__(16) float2 S[2 * FB * BUF];
     const int tile = blockIdx.x, sl = blockIdx.y;
     const int4 T = p.tiles[tile];
     const int wx0 = T.x, wy0 = T.y, vx0 = T.z, vy0 = T.w;
@@ -112,56 +168,64 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
     }
     const bool active = kkmask != 0;
 
-    const size_t box = (size_t)p.box_rows * p.box_pitch;
-    const size_t sbase = (size_t)sl * F * box;
-    float2 pre[LPT];
-#pragma unroll
-    for (int i = 0; i < LPT; ++i)
-        pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, sbase + src[i]) : make_float2(0.f, 0.f);
-
     float2 acc[4][smi::VBX];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int kk = 0; kk < smi::VBX; ++kk) acc[j][kk] = make_float2(0.f, 0.f);
 
-    for (int f = 0; f < F; ++f) {
-        float2* Sb = S + (f & 1) * BUF;
+    const size_t box = (size_t)p.box_rows * p.box_pitch;
+    const size_t sbase = (size_t)sl * F * box;
+    if (ASYNC) {
+        const float2* sp = reinterpret_cast<const float2*>(spec) + sbase;
+        const int nst = (F + FB - 1) / FB;
+        auto issue = [&](int st) {
+            if (st < nst) {
+                float2* Sb = S + (st & 1) * FB * BUF;
 #pragma unroll
-        for (int i = 0; i < LPT; ++i)
-            if (dst[i] >= 0) Sb[dst[i]] = pre[i];
-        __syncthreads();
-        if (f + 1 < F) {
-            const size_t fb = sbase + (size_t)(f + 1) * box;
+                for (int ff = 0; ff < FB; ++ff) {
+                    const int f = st * FB + ff;
+                    if (f < F) {
 #pragma unroll
-            for (int i = 0; i < LPT; ++i)
-                pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, fb + src[i]) : make_float2(0.f, 0.f);
-        }
-        if (active) {
-            float2 a[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float2 t = Sb[OFF_W + wyl * PW + 4 * gx + j];
-                a[j] = make_float2(t.x, -t.y);          // conj I(w)
-            }
-            float2 c[11];
-            const float2* up = Sb + OFF_U + (wyl - warp + smi::VBY - 1) * PU + 4 * gx;
-#pragma unroll
-            for (int m = 0; m < 11; ++m) c[m] = up[m];  // I(w - v), m = j - kk + 7
-            const float2* vp = Sb + OFF_V + warp * smi::VBX;
-#pragma unroll
-            for (int kk = 0; kk < smi::VBX; ++kk) {
-                if (!(kkmask & (1u << kk))) continue;    // warp-uniform
-                const float2 b = vp[kk];                 // I(v), warp broadcast
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float2 u = c[j - kk + 7];
-                    const float px = fmaf(u.x, b.x, -u.y * b.y);
-                    const float py = fmaf(u.x, b.y, u.y * b.x);
-                    acc[j][kk].x = fmaf(px, a[j].x, fmaf(-py, a[j].y, acc[j][kk].x));
-                    acc[j][kk].y = fmaf(px, a[j].y, fmaf(py, a[j].x, acc[j][kk].y));
+                        for (int i = 0; i < LPT; ++i)
+                            if (dst[i] >= 0)
+                                cp_async8(Sb + ff * BUF + dst[i], sp + (size_t)f * box + (src[i] >= 0 ? src[i] : 0),
+                                          src[i] >= 0 ? 8 : 0);
+                    }
                 }
             }
+            asm volatile("cp.async.commit_group;");
+        };
+        issue(0);
+        for (int st = 0; st < nst; ++st) {
+            asm volatile("cp.async.wait_group 0;");
+            __syncthreads();          // stage st visible to all; stage st-1 fully consumed
+            issue(st + 1);
+            if (!active) continue;
+            const float2* Sst = S + (st & 1) * FB * BUF;
+#pragma unroll
+            for (int ff = 0; ff < FB; ++ff)
+                if (st * FB + ff < F) accumulate_frame(Sst + ff * BUF, wyl, gx, warp, kkmask, acc);
+        }
+        asm volatile("cp.async.wait_group 0;");
+    } else {
+        float2 pre[LPT];
+#pragma unroll
+        for (int i = 0; i < LPT; ++i)
+            pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, sbase + src[i]) : make_float2(0.f, 0.f);
+        for (int f = 0; f < F; ++f) {
+            float2* Sb = S + (f & 1) * BUF;
+#pragma unroll
+            for (int i = 0; i < LPT; ++i)
+                if (dst[i] >= 0) Sb[dst[i]] = pre[i];
+            __syncthreads();
+            if (f + 1 < F) {
+                const size_t fb = sbase + (size_t)(f + 1) * box;
+#pragma unroll
+                for (int i = 0; i < LPT; ++i)
+                    pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, fb + src[i]) : make_float2(0.f, 0.f);
+            }
+            if (active) accumulate_frame(Sb, wyl, gx, warp, kkmask, acc);
         }
     }
 
@@ -178,7 +242,6 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
                                acc[j][2 * q + 1].x * sc, acc[j][2 * q + 1].y * sc);
     }
 }
-
 
 }  // namespace
 

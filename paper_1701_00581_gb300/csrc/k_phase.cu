@@ -6,11 +6,11 @@
 // exp(i phi(w)).  One CTA per subfield walks the rings of equal |w|^2 in
 // ascending order (points of one ring never depend on each other).  The
 // ring's work is a list of (point, bispectrum tile) items; the 16 warps
-// take items round-robin, four at a time so that their B loads are in
+// take items round-robin, eight at a time so that their B loads are in
 // flight together, and sum exp(i(phi(w-v) + phi(v))) conj B over the
 // offsets of the tile (FP32 products and item sums; GB300's FP64 rate is a
-// small fraction of its FP32 rate) into one partial per item.
-// Then one thread per point adds its partials in a fixed order and stores
+// small fraction of its FP32 rate) into one partial per item.  Then one
+// warp per point adds its partials in FP64 along a fixed tree and stores
 // z(w) = S / |S|: the result does not depend on scheduling.  The known
 // phasors live in shared memory (FP32 copy for the products); the FP64
 // result goes to HBM.
@@ -25,13 +25,6 @@ using smi::TILE_V;
 constexpr int PH_THREADS = 512;
 constexpr int PH_WARPS = PH_THREADS / 32;
 
-__device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2i, int R2) {
-    const int w2 = wx * wx + wy * wy, v2 = vx * vx + vy * vy;
-    const int ux = wx - vx, uy = wy - vy, u2 = ux * ux + uy * uy;
-    const bool inH = wy > 0 || (wy == 0 && wx > 0);
-    return inH && w2 >= 2 && w2 <= r2i && v2 > 0 && v2 <= R2 && v2 < w2 && u2 < w2;
-}
-
 // z of any frequency from the half-box copy (row 0 holds both signs).
 __device__ __forceinline__ float2 zget(const float2* zs, int pitch, int K, int kx, int ky) {
     if (ky >= 0) return zs[ky * pitch + kx + K];
@@ -39,7 +32,32 @@ __device__ __forceinline__ float2 zget(const float2* zs, int pitch, int K, int k
     return make_float2(t.x, -t.y);
 }
 
-constexpr int PH_UNROLL = 8;          // items in flight per warp
+constexpr int PH_ITEMS = 8;           // items per warp batch (all loads in flight together)
+
+// Eight per-lane values -> eight warp sums, by recursive halving: after the
+// exchanges at distances 16, 8 and 4 each lane holds one item's partial sum
+// over 8 lanes (item = lane >> 2), then two xor steps finish it.  18 shuffles
+// instead of 8 full reductions (80).
+__device__ __forceinline__ float2 reduce8(float2 (&s)[PH_ITEMS], int lane) {
+#pragma unroll
+    for (int lvl = 0, o = 16, n = PH_ITEMS / 2; lvl < 3; ++lvl, o >>= 1, n >>= 1) {
+        const bool hi = lane & o;
+#pragma unroll
+        for (int q = 0; q < n; ++q) {
+            const float2 keep = hi ? s[q + n] : s[q];
+            const float2 give = hi ? s[q] : s[q + n];
+            s[q].x = keep.x + __shfl_xor_sync(0xffffffffu, give.x, o);
+            s[q].y = keep.y + __shfl_xor_sync(0xffffffffu, give.y, o);
+        }
+    }
+    float2 r = s[0];
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) {
+        r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
+        r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+    }
+    return r;
+}
 
 __global__ void __launch_bounds__(PH_THREADS, 2)
 k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
@@ -47,8 +65,8 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K, pitch = p.box_pitch;
     const size_t hb = (size_t)p.hb_rows * pitch;
-    double2* part = reinterpret_cast<double2*>(smem);              // [max_ring_items]
-    float2* zs = reinterpret_cast<float2*>(part + p.max_ring_items); // [hb]
+    float2* part = reinterpret_cast<float2*>(smem);                      // [max_ring_items]
+    float2* zs = reinterpret_cast<float2*>(smem) + ((p.max_ring_items + 1) & ~1);  // [hb]
     const int sl = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     double2* zo = z + (size_t)sl * hb;
     for (int e = tid; e < (int)hb; e += PH_THREADS) zs[e] = make_float2(0.f, 0.f);
@@ -72,37 +90,29 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
     }
     __syncthreads();
 
-    const int R2 = p.R * p.R;
     const bool unit = p.weight == SM_W_UNIT;
     const float2* Bs = B + (size_t)sl * p.n_tiles * TILE_PAIRS;
-    constexpr int NH = TILE_V / 32;        // offsets per lane per item
-    // one batch = up to PH_UNROLL items of a warp; B does not depend on the
-    // phases, so the next ring's first batch is loaded before the barriers.
-    // Per item: w and the tile's offset origin packed as four signed bytes
-    // (the plan keeps |coordinates| < 128), the B value of this lane's offset, and a
-    // bit saying whether that (w, v) pair is read.
-    static_assert(NH == 1, "one offset per lane per item");
-    float2 bv[PH_UNROLL];
-    unsigned pk[PH_UNROLL];
+    // A batch is up to PH_ITEMS items of one warp.  Each item comes from the
+    // plan as (w and offset origin as four signed bytes, B offset, mask of
+    // lanes whose (w, v) pair is read); the lane's B value is loaded at once.
+    // B does not depend on the phases, so the next ring's first batch is
+    // loaded before the ring's barriers.
+    float2 bv[PH_ITEMS];
+    unsigned pk[PH_ITEMS];
     unsigned okm = 0;
     auto load_batch = [&](int base, int i1) {
         okm = 0;
 #pragma unroll
-        for (int q = 0; q < PH_UNROLL; ++q) {
+        for (int q = 0; q < PH_ITEMS; ++q) {
             const int it = base + q * PH_WARPS;
             bv[q] = make_float2(0.f, 0.f);
             pk[q] = 0;
             if (it < i1) {
-                const int2 item = p.items[it];
-                const int2 w = p.points[item.x];
-                const int4 T = p.tiles[item.y];
-                pk[q] = (unsigned)(w.x & 255) | ((unsigned)(w.y & 255) << 8) |
-                        ((unsigned)(T.z & 255) << 16) | ((unsigned)(T.w & 255) << 24);
-                const int wxl = (w.x + K) % smi::WBX, wyl = w.y % smi::WBY;
-                const float2* bp = Bs + (size_t)item.y * TILE_PAIRS + (wyl * smi::WBX + wxl) * TILE_V;
-                if (pair_used(w.x, w.y, T.z + (lane % smi::VBX), T.w + (lane / smi::VBX), p.r2i, R2)) {
+                const int4 item = p.items[it];
+                pk[q] = (unsigned)item.x;
+                if ((unsigned)item.z & (1u << lane)) {
                     okm |= 1u << q;
-                    bv[q] = bp[lane];
+                    bv[q] = Bs[(size_t)item.y + lane];
                 }
             }
         }
@@ -110,16 +120,13 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
     load_batch(p.ring_items[0] + warp, p.ring_items[1]);
     for (int r = 0; r < p.n_rings; ++r) {
         const int i0 = p.ring_items[r], i1 = p.ring_items[r + 1];
-        // (1) every (point, tile) item of the ring: warp-summed phasor terms
-        for (int base = i0 + warp; base < i1; base += PH_WARPS * PH_UNROLL) {
+        // (1) items: FP32 products, one term per lane, FP32 item sums
+        for (int base = i0 + warp; base < i1; base += PH_WARPS * PH_ITEMS) {
             if (base != i0 + warp) load_batch(base, i1);
+            float2 t[PH_ITEMS];
 #pragma unroll
-            for (int q = 0; q < PH_UNROLL; ++q) {
-                const int it = base + q * PH_WARPS;
-                if (it >= i1) break;                       // warp-uniform
-                // FP32 products and per-item sums (one term per lane); the
-                // per-point sum and the phasor state are FP64
-                float sx = 0.f, sy = 0.f;
+            for (int q = 0; q < PH_ITEMS; ++q) {
+                t[q] = make_float2(0.f, 0.f);
                 if (okm & (1u << q)) {
                     const int wx = (signed char)(pk[q] & 255), wy = (signed char)((pk[q] >> 8) & 255);
                     const int vx = (signed char)((pk[q] >> 16) & 255) + (lane % smi::VBX);
@@ -139,37 +146,41 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
                             tx = ty = 0.f;
                         }
                     }
-                    sx = tx;
-                    sy = ty;
+                    t[q] = make_float2(tx, ty);
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-                }
-                if (lane == 0) part[it - i0] = make_double2((double)sx, (double)sy);
             }
+            const float2 sum = reduce8(t, lane);
+            const int q = lane >> 2, it = base + q * PH_WARPS;
+            if ((lane & 3) == 0 && it < i1) part[it - i0] = sum;
         }
         if (r + 1 < p.n_rings) load_batch(i1 + warp, p.ring_items[r + 2]);
         __syncthreads();
-        // (2) one thread per point: sum its items in order, normalise
+        // (2) one warp per point: FP64 sum of its items (fixed tree), normalise
         const int pe = p.ring_start[r + 1];
-        for (int pt = p.ring_start[r] + tid; pt < pe; pt += PH_THREADS) {
-            double sx = 0.0, sy = 0.0;
+        for (int pt = p.ring_start[r] + warp; pt < pe; pt += PH_WARPS) {
             const int a0 = p.point_items[pt], a1 = p.point_items[pt + 1];
-            for (int a = a0; a < a1; ++a) {
-                sx += part[a - i0].x;
-                sy += part[a - i0].y;
+            double sx = 0.0, sy = 0.0;
+            for (int a = a0 + lane; a < a1; a += 32) {
+                const float2 v = part[a - i0];
+                sx += (double)v.x;
+                sy += (double)v.y;
             }
-            const int2 w = p.points[pt];
-            const double n = hypot(sx, sy);
-            const double2 zz = n > 0 ? make_double2(sx / n, sy / n) : make_double2(1.0, 0.0);
-            const int o = w.y * pitch + w.x + K;
-            zs[o] = make_float2((float)zz.x, (float)zz.y);
-            zo[o] = zz;
-            if (w.y == 0) {
-                zs[-w.x + K] = make_float2((float)zz.x, -(float)zz.y);
-                zo[-w.x + K] = make_double2(zz.x, -zz.y);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+            if (lane == 0) {
+                const int2 w = p.points[pt];
+                const double n = hypot(sx, sy);
+                const double2 zz = n > 0 ? make_double2(sx / n, sy / n) : make_double2(1.0, 0.0);
+                const int o = w.y * pitch + w.x + K;
+                zs[o] = make_float2((float)zz.x, (float)zz.y);
+                zo[o] = zz;
+                if (w.y == 0) {
+                    zs[-w.x + K] = make_float2((float)zz.x, -(float)zz.y);
+                    zo[-w.x + K] = make_double2(zz.x, -zz.y);
+                }
             }
         }
         __syncthreads();
@@ -181,7 +192,7 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
 namespace smk {
 
 size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items) {
-    return (size_t)max_ring_items * sizeof(double2) + (size_t)hb_rows * box_pitch * sizeof(float2);
+    return (size_t)((max_ring_items + 1) & ~1) * sizeof(float2) + (size_t)hb_rows * box_pitch * sizeof(float2);
 }
 
 cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M,

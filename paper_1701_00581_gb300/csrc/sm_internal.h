@@ -21,6 +21,7 @@ constexpr int TILE_W = WBX * WBY;            // 128 targets
 constexpr int TILE_V = VBX * VBY;            // 32 offsets
 constexpr int TILE_PAIRS = TILE_W * TILE_V;  // 4096 (w, v) slots
 constexpr int BISPEC_THREADS = 32 * VBY;     // one warp per offset row
+static_assert(TILE_V == 32, "a tile row of offsets maps onto the 32 lanes of a warp");
 
 constexpr float FP16_SCALE = 16384.0f;       // |I_n| <= 1 -> fits half with margin
 constexpr float FP16_INV_SCALE = 1.0f / 16384.0f;
@@ -48,7 +49,8 @@ struct PlanDev {
     const int* wb_tiles;
     // phase recursion work items: (point, tile) pairs holding at least one
     // pair the point reads, grouped by point, points in ring order
-    const int2* items;          // [n_items] (point index, tile id)
+    const int4* items;          // [n_items] packed (w, offset origin) bytes, B offset
+                                //   within the subfield, mask of lanes whose pair is read
     const int* ring_items;      // [n_rings + 1] first item of each ring
     const int* point_items;     // [n_points + 1] first item of each point
     int n_items, max_ring_items;

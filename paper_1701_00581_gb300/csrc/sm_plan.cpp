@@ -241,11 +241,15 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         for (int ti = pl->wb_start[wb]; ti < pl->wb_start[wb + 1]; ++ti) {
             const int t = pl->wb_tiles[ti];
             const int4 T = pl->tiles[t];
-            bool any = false;
-            for (int c = 0; c < VBY && !any; ++c)
-                for (int e = 0; e < VBX && !any; ++e)
-                    any = pair_used_host(wx, wy, T.z + e, T.w + c, r2i, R * R);
-            if (any) pl->items.push_back(make_int2(pi, t));
+            unsigned mask = 0;
+            for (int l = 0; l < TILE_V; ++l)
+                if (pair_used_host(wx, wy, T.z + l % VBX, T.w + l / VBX, r2i, R * R)) mask |= 1u << l;
+            if (!mask) continue;
+            const unsigned packed = (unsigned)(wx & 255) | ((unsigned)(wy & 255) << 8) |
+                                    ((unsigned)(T.z & 255) << 16) | ((unsigned)(T.w & 255) << 24);
+            const int wxl = (wx + K) % WBX, wyl = wy % WBY;
+            const int boff = t * TILE_PAIRS + (wyl * WBX + wxl) * TILE_V;
+            pl->items.push_back(make_int4((int)packed, boff, (int)mask, 0));
         }
     }
     pl->point_items[d.n_points] = (int)pl->items.size();
@@ -276,7 +280,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         {pl->wb_start.data(), pl->wb_start.size() * sizeof(int), 0},
         {pl->wb_tiles.data(), pl->wb_tiles.size() * sizeof(int), 0},
         {t0.data(), t0.size() * sizeof(double), 0},
-        {pl->items.data(), pl->items.size() * sizeof(int2), 0},
+        {pl->items.data(), pl->items.size() * sizeof(int4), 0},
         {pl->ring_items.data(), pl->ring_items.size() * sizeof(int), 0},
         {pl->point_items.data(), pl->point_items.size() * sizeof(int), 0},
         {winft.data(), winft.size() * sizeof(float2), 0},
@@ -304,7 +308,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.wb_start = (const int*)at(8);
     d.wb_tiles = (const int*)at(9);
     d.t0 = (const double*)at(10);
-    d.items = (const int2*)at(11);
+    d.items = (const int4*)at(11);
     d.ring_items = (const int*)at(12);
     d.point_items = (const int*)at(13);
     d.winft = (const float2*)at(14);

@@ -17,7 +17,7 @@ struct sm_plan {
     std::vector<int> wb_start, wb_tiles;
     std::vector<int> ring_start;
     std::vector<int2> points;
-    std::vector<int2> items;
+    std::vector<int4> items;
     std::vector<int> ring_items, point_items;
     long long n_pairs = 0;
     int n_U = 0, n_V = 0;

@@ -111,7 +111,10 @@ def gpu_run(plan, frames_np: np.ndarray, stf_np: np.ndarray, chunk: int = None):
         torch.cuda.synchronize()
         v = plan.views(ws, lay, F, ns)
         for k in res:
-            res[k].append(v[k].cpu().numpy().copy())
+            t = v[k]
+            if t.dtype in (torch.float16, torch.bfloat16):
+                t = t.float()
+            res[k].append(t.cpu().numpy().copy())
     plan.stage_mosaic(ws, lay, out, valid)
     torch.cuda.synchronize()
     v = plan.views(ws, lay, F, 1)
