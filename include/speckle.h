@@ -211,7 +211,10 @@ int sm_model_stf(const sm_channel* ch, int F, const double* d_over_r0, double* s
 
 /* ======================================================================== *
  *  Serving engine: bursts from several channels admitted as device slots   *
- *  free up, processed concurrently, results polled by ticket.              *
+ *  free up, processed concurrently, results polled by ticket.  Each slot   *
+ *  has its own stream; a burst's stage sequence is captured once as a CUDA *
+ *  graph per (channel, F, frame type, arena offset, slot) and replayed for *
+ *  later bursts with the same key.                                         *
  * ======================================================================== */
 typedef struct sm_handle sm_handle;
 

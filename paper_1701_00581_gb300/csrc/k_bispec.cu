@@ -67,9 +67,9 @@ __device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2
     return inH && w2 >= 2 && w2 <= r2i && v2 > 0 && v2 <= R2 && v2 < w2 && u2 < w2;
 }
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int bytes) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(sa), "l"(gmem), "r"(bytes));
+// 8-byte asynchronous copy global -> shared; bytes = 0 zero-fills.
+__device__ __forceinline__ void cp_async8(unsigned smem_addr, const void* gmem, int bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(smem_addr), "l"(gmem), "r"(bytes));
 }
 
 // One frame of the thread's 4 x 8 pairs from the staged rectangles.
@@ -179,18 +179,28 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
     if (ASYNC) {
         const float2* sp = reinterpret_cast<const float2*>(spec) + sbase;
         const int nst = (F + FB - 1) / FB;
+        // per element: global source (frame 0), shared destination (buffer 0)
+        // and copy size (0 = zero fill outside the box), fixed for the CTA
+        const float2* gsrc[LPT];
+        unsigned sdst[LPT];
+        int nb[LPT];
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) {
+            gsrc[i] = sp + (src[i] >= 0 ? src[i] : 0);
+            sdst[i] = (unsigned)__cvta_generic_to_shared(S + (dst[i] >= 0 ? dst[i] : 0));
+            nb[i] = src[i] >= 0 ? 8 : 0;
+        }
         auto issue = [&](int st) {
             if (st < nst) {
-                float2* Sb = S + (st & 1) * FB * BUF;
 #pragma unroll
                 for (int ff = 0; ff < FB; ++ff) {
                     const int f = st * FB + ff;
                     if (f < F) {
+                        const unsigned soff = (unsigned)(((st & 1) * FB + ff) * BUF * sizeof(float2));
+                        const size_t goff = (size_t)f * box;
 #pragma unroll
                         for (int i = 0; i < LPT; ++i)
-                            if (dst[i] >= 0)
-                                cp_async8(Sb + ff * BUF + dst[i], sp + (size_t)f * box + (src[i] >= 0 ? src[i] : 0),
-                                          src[i] >= 0 ? 8 : 0);
+                            if (dst[i] >= 0) cp_async8(sdst[i] + soff, gsrc[i] + goff, nb[i]);
                     }
                 }
             }

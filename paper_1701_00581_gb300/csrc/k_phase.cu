@@ -8,12 +8,11 @@
 // ring's work is a list of (point, bispectrum tile) items; the 16 warps
 // take items round-robin, eight at a time so that their B loads are in
 // flight together, and sum exp(i(phi(w-v) + phi(v))) conj B over the
-// offsets of the tile (FP32 products and item sums; GB300's FP64 rate is a
-// small fraction of its FP32 rate) into one partial per item.  Then one
-// warp per point adds its partials in FP64 along a fixed tree and stores
-// z(w) = S / |S|: the result does not depend on scheduling.  The known
-// phasors live in shared memory (FP32 copy for the products); the FP64
-// result goes to HBM.
+// offsets of the tile into one partial per item.  Then one warp per point
+// adds its partials along a fixed tree and stores z(w) = S / |S|: the
+// result does not depend on scheduling.  Arithmetic is FP32 (GB300's FP64
+// unit is shared by the SM's warps and a small fraction of its FP32 rate);
+// the known phasors live in shared memory and the result is stored as FP64.
 #include "sm_internal.h"
 
 namespace {
@@ -155,15 +154,18 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         }
         if (r + 1 < p.n_rings) load_batch(i1 + warp, p.ring_items[r + 2]);
         __syncthreads();
-        // (2) one warp per point: FP64 sum of its items (fixed tree), normalise
+        // (2) one warp per point: sum of its items along a fixed shuffle
+        // tree, then z = S / |S|.  FP32: the phasors feed the next rings in
+        // FP32 anyway, and GB300's shared FP64 unit serialised this step
+        // across warps when it ran in FP64.  The stored state is FP64.
         const int pe = p.ring_start[r + 1];
         for (int pt = p.ring_start[r] + warp; pt < pe; pt += PH_WARPS) {
             const int a0 = p.point_items[pt], a1 = p.point_items[pt + 1];
-            double sx = 0.0, sy = 0.0;
+            float sx = 0.f, sy = 0.f;
             for (int a = a0 + lane; a < a1; a += 32) {
                 const float2 v = part[a - i0];
-                sx += (double)v.x;
-                sy += (double)v.y;
+                sx += v.x;
+                sy += v.y;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -172,14 +174,18 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
             }
             if (lane == 0) {
                 const int2 w = p.points[pt];
-                const double n = hypot(sx, sy);
-                const double2 zz = n > 0 ? make_double2(sx / n, sy / n) : make_double2(1.0, 0.0);
+                const float n2 = sx * sx + sy * sy;
+                float2 zz = make_float2(1.f, 0.f);
+                if (n2 > 0.f) {
+                    const float inv = rsqrtf(n2);
+                    zz = make_float2(sx * inv, sy * inv);
+                }
                 const int o = w.y * pitch + w.x + K;
-                zs[o] = make_float2((float)zz.x, (float)zz.y);
-                zo[o] = zz;
+                zs[o] = zz;
+                zo[o] = make_double2((double)zz.x, (double)zz.y);
                 if (w.y == 0) {
-                    zs[-w.x + K] = make_float2((float)zz.x, -(float)zz.y);
-                    zo[-w.x + K] = make_double2(zz.x, -zz.y);
+                    zs[-w.x + K] = make_float2(zz.x, -zz.y);
+                    zo[-w.x + K] = make_double2((double)zz.x, -(double)zz.y);
                 }
             }
         }
