@@ -133,12 +133,15 @@ __device__ __forceinline__ void store_spec(void* spec, size_t idx, float2 v) {
 
 constexpr int FFT_THREADS = 256;
 constexpr int FFT_WARPS = FFT_THREADS / 32;
+// Forward transforms: 32 groups of 16 threads for N >= 128 (one CTA per SM
+// fits in shared memory, so latency is hidden by warps within the CTA).
+template <int N> struct SpecThreads { static constexpr int T = N >= 128 ? 512 : 256; };
 
 // Thread groups of the four-step transform: G threads per transform.
 template <int N> struct Grp {
     static constexpr int P = Split<N>::P, Q = Split<N>::Q;
     static constexpr int G = P > Q ? P : Q;
-    static constexpr int NG = FFT_THREADS / G;                       // groups per CTA
+    static constexpr int NG = SpecThreads<N>::T / G;                 // groups per CTA
     static constexpr int TB = (Q * (P + 1) > N ? Q * (P + 1) : N);   // exchange buffer
 };
 
@@ -166,11 +169,12 @@ __host__ __device__ constexpr size_t fft_smem(int N, int K) {
 // read off the row transforms' DC terms, mu * window is removed through the
 // window's own transform, and the K+1 non-negative columns are transformed.
 template <int N, typename TIn, int PREC>
-__global__ void __launch_bounds__(FFT_THREADS, 1)
+__global__ void __launch_bounds__(SpecThreads<N>::T, 1)
 k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __restrict__ spec,
           float* __restrict__ flux, float* __restrict__ mu) {
     using GP = Grp<N>;
     constexpr int P = GP::P, Q = GP::Q, G = GP::G, NG = GP::NG, TB = GP::TB;
+    constexpr int TS = SpecThreads<N>::T, WS = TS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     const int K1 = p.K + 1, CP = N + 1;
     float2* C = reinterpret_cast<float2*>(smem);
@@ -187,12 +191,12 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
     float2* T = scratch + grp * TB;
     const int4 sb = p.subs[s];
     const int x0 = sb.x, y0 = sb.y, w = sb.z, h = sb.w;
-    for (int i = tid; i < N; i += FFT_THREADS) {
+    for (int i = tid; i < N; i += TS) {
         stw[i] = p.tw[i];
         swx[i] = p.winx[(size_t)s * N + i];
         swy[i] = p.winy[(size_t)s * N + i];
     }
-    for (int i = tid; i < K1; i += FFT_THREADS) swf[i] = p.winft[(size_t)s * K1 + i];
+    for (int i = tid; i < K1; i += TS) swf[i] = p.winft[(size_t)s * K1 + i];
     __syncthreads();
 
     const TIn* fr = frames + (size_t)f * p.H * p.W + (size_t)y0 * p.W + x0;
@@ -208,8 +212,8 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
             raw[1][n2] = inx && y2 < h ? load_sample(fr + (size_t)y2 * p.W + x) : 0.f;
         }
     };
-    fetch(grp);
     for (int pr0 = 0; pr0 < N / 2; pr0 += NG) {
+        fetch(pr0 + grp);
         const int pr = pr0 + grp, y1 = 2 * pr, y2 = y1 + 1;
         float2 v[Q], X[P];
 #pragma unroll
@@ -217,7 +221,6 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
             const float wx = swx[(g + P * n2) & (N - 1)];
             v[n2] = make_float2(wx * swy[y1] * raw[0][n2], wx * swy[y2] * raw[1][n2]);
         }
-        if (pr0 + NG < N / 2) fetch(pr + NG);
         four_step<N, false>(v, X, T, stw, g);
         if (g < Q) {
 #pragma unroll
@@ -235,17 +238,17 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
 
     // windowed mean from the DC terms of the row transforms
     double dacc = 0.0;
-    for (int y = tid; y < N; y += FFT_THREADS) dacc += (double)C[y].x;
+    for (int y = tid; y < N; y += TS) dacc += (double)C[y].x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
     if (lane == 0) red[warp] = dacc;
     __syncthreads();
     double tot = 0.0;
-    for (int i = 0; i < FFT_WARPS; ++i) tot += red[i];
+    for (int i = 0; i < WS; ++i) tot += red[i];
     const double wsum = p.winsum[s];
     const float mean = (float)(tot / wsum);
     // remove mean * window: row transform of w_x(x) w_y(y) mu is mu w_y(y) Wx(kx)
-    for (int e = tid; e < K1 * h; e += FFT_THREADS) {
+    for (int e = tid; e < K1 * h; e += TS) {
         const int kx = e / h, y = e - kx * h;
         const float a = mean * swy[y];
         float2& c = C[kx * CP + y];
@@ -275,7 +278,7 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
     const float inv = (float)(1.0 / fl);
     const size_t base = ((size_t)sl * F + f) * p.box_rows * p.box_pitch;
     const int nbox = p.box_rows * p.box_cols;
-    for (int e = tid; e < nbox; e += FFT_THREADS) {
+    for (int e = tid; e < nbox; e += TS) {
         const int row = e / p.box_cols, col = e - row * p.box_cols;
         const int ky = row - p.R, kx = col - p.K;
         float2 v;
@@ -396,7 +399,7 @@ cudaError_t spectra_n(const PlanDev& p, const void* frames, int frame_type, int 
         e = cudaFuncSetAttribute(k_spectra<N, TIN, PREC>,                                       \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);         \
         if (e != cudaSuccess) return e;                                                         \
-        k_spectra<N, TIN, PREC><<<grid, FFT_THREADS, sm, st>>>(                                 \
+        k_spectra<N, TIN, PREC><<<grid, SpecThreads<N>::T, sm, st>>>(                                 \
             p, reinterpret_cast<const TIN*>(frames), F, sub0, spec, flux, mu);                  \
     } while (0)
     if (frame_type == SM_U16) {

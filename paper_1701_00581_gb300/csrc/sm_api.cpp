@@ -1,11 +1,14 @@
 // C ABI: workspace layout, stage entry points, the whole-burst path and the
 // serving engine.  No exception crosses the ABI; every call returns a status.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <string>
@@ -265,18 +268,33 @@ struct sm_handle {
     std::vector<int> chunk;               // subfields per chunk, per channel
     std::vector<cudaStream_t> streams;
     std::vector<bool> stream_busy;
+    std::vector<double*> stf_pinned;      // per slot: pinned host staging of the STF table
     Arena arena;
     void* dmem = nullptr;
     std::mutex mu;
     std::map<uint64_t, Job> jobs;
     uint64_t next_ticket = 1;
     Clock::time_point t0;
+    // Instantiated launch graphs of whole bursts, keyed by (channel, F,
+    // arena offset, stream slot): every pointer a burst's kernels take is
+    // fixed by that key, so a burst that lands where an earlier one did
+    // replays its graph instead of issuing the launches again.
+    std::map<std::tuple<int, int, size_t, int>, cudaGraphExec_t> graphs;
 };
 
 namespace {
 
 double ms_since(const Clock::time_point& t0) {
     return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+// Diagnostics on stderr: SM_LOG=2 prints the phase timings of every submit.
+int log_level() {
+    static const int lvl = [] {
+        const char* e = getenv("SM_LOG");
+        return e ? atoi(e) : 0;
+    }();
+    return lvl;
 }
 
 // Device bytes one burst of channel c holds: frames, workspace, mosaic, mask, STF.
@@ -296,6 +314,43 @@ void finish_job(sm_handle* h, Job& j) {
     j.bytes = 0;
     if (j.slot >= 0) h->stream_busy[j.slot] = false;
     j.slot = -1;
+}
+
+}  // namespace
+
+namespace {
+
+// Launch one burst's stage sequence on its slot stream through a cached
+// CUDA graph (captured on first use of the key).  The frame type is part of
+// the captured kernels, so it joins the key through the channel's F slot.
+int launch_burst(sm_handle* h, const sm_burst* b, const Job& j, const void* d_frames, const double* d_stf,
+                 void* ws, sm_workspace_layout& lay, cudaStream_t st) {
+    const auto key = std::make_tuple(b->channel, b->F * 2 + (b->frame_type == SM_F32 ? 1 : 0), j.off, j.slot);
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        auto it = h->graphs.find(key);
+        if (it != h->graphs.end()) exec = it->second;
+    }
+    if (!exec) {
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        const int rc = sm_reconstruct(h->plans[b->channel], d_frames, b->frame_type, b->F, d_stf,
+                                      h->chunk[b->channel], ws, &lay, j.d_out, j.d_valid, st);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(st, &graph);
+        if (rc != SM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        std::lock_guard<std::mutex> lk(h->mu);
+        h->graphs[key] = exec;
+    }
+    return ret(cudaGraphLaunch(exec, st), "cudaGraphLaunch");
 }
 
 }  // namespace
@@ -343,6 +398,12 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
         if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaStreamCreate"); }
         h->streams.push_back(s);
         h->stream_busy.push_back(false);
+        size_t nmax = 0;
+        for (const auto& c : h->ch) nmax = std::max(nmax, (size_t)c.N * c.N);
+        double* pin = nullptr;
+        e = cudaHostAlloc((void**)&pin, nmax * sizeof(double), cudaHostAllocDefault);
+        if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaHostAlloc"); }
+        h->stf_pinned.push_back(pin);
     }
     *out = h;
     return SM_OK;
@@ -355,12 +416,14 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     if (b->F < 1 || b->F > ch.max_frames || !b->frames || !b->out) { set_error("bad burst"); return SM_EINVAL; }
     if (b->frame_type != SM_U16 && b->frame_type != SM_F32) { set_error("bad frame_type"); return SM_EINVAL; }
     if (!b->stf && !b->d_over_r0) { set_error("need stf or d_over_r0"); return SM_EINVAL; }
+    const auto t_in = Clock::now();
     std::vector<double> stf;
     if (!b->stf) {
         stf.resize((size_t)ch.N * ch.N);
         int rc = sm_model_stf(&ch, b->F, b->d_over_r0, stf.data());
         if (rc) return rc;
     }
+    const double t_stf = ms_since(t_in);
     const double* stf_src = b->stf ? b->stf : stf.data();
     DeviceGuard g(h->cfg.device);
     sm_workspace_layout lay;
@@ -402,16 +465,22 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
         else
             e = cudaMemcpyAsync(d_frames, b->frames, fbytes, cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_stf, stf_src, (size_t)ch.N * ch.N * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        // from pinned staging: a pageable source would make the copy wait
+        // behind the frame transfer and other pageable traffic
+        double* pin = h->stf_pinned[j.slot];
+        std::memcpy(pin, stf_src, (size_t)ch.N * ch.N * sizeof(double));
+        e = cudaMemcpyAsync(d_stf, pin, (size_t)ch.N * ch.N * sizeof(double), cudaMemcpyHostToDevice, st);
+    }
+    const double t_copy = ms_since(t_in);
     if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(j.ev_start);   // input staged: caller may reuse frames
+    const double t_staged = ms_since(t_in);
     int rc = SM_OK;
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "staging burst");
     } else {
-        rc = sm_reconstruct(h->plans[b->channel], d_frames, b->frame_type, b->F, d_stf, h->chunk[b->channel], ws,
-                            &lay, j.d_out, j.d_valid, st);
+        rc = launch_burst(h, b, j, d_frames, d_stf, ws, lay, st);
         if (rc == SM_OK) {
             e = cudaEventRecord(j.ev_done, st);
             if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
@@ -424,6 +493,10 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
         return rc;
     }
     j.t_submit = ms_since(h->t0);
+    if (log_level() >= 2)
+        fprintf(stderr, "[speckle] submit ticket %llu ch %d slot %d off %zu: stf %.2f ms, copies issued %.2f ms, "
+                        "staged %.2f ms, launched %.2f ms\n", (unsigned long long)j.ticket, j.channel, j.slot, j.off,
+                t_stf, t_copy, t_staged, ms_since(t_in));
     *ticket = j.ticket;
     h->jobs[j.ticket] = j;
     return SM_OK;
@@ -493,7 +566,10 @@ extern "C" int sm_close(sm_handle* h) {
         for (auto& kv : h->jobs) finish_job(h, kv.second);
         h->jobs.clear();
     }
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
     for (auto s : h->streams) cudaStreamDestroy(s);
+    for (auto p : h->stf_pinned) cudaFreeHost(p);
     if (h->dmem) cudaFree(h->dmem);
     for (auto* p : h->plans) sm_plan_destroy(p);
     delete h;

@@ -223,3 +223,31 @@ def test_invalid_stage_arguments_fail_cleanly(ragged):
         plan.layout(plan.ch.max_frames + 1, 1)
     with pytest.raises(SpeckleError):
         plan.stage_amplitude(1, None, ws, lay)
+
+
+@pytest.mark.parametrize("name,kw", [("unit_weights", dict(phase_weight=1)),
+                                     ("overlap75", dict(stride=16)),
+                                     ("chain_R1", dict(R=1))])
+def test_method_variants_match_oracle(torch, name, kw):
+    """Unit-modulus phase terms, a 75 % overlap grid (stride N/4, as in the
+    paper's own 1110-cube layout) and R = 1 (single-path recursion), each
+    against the oracle run with the same parameters."""
+    from paper_1701_00581_gb300 import Channel, Plan
+    c = CS.case("ragged")
+    sp = c["spec"]
+    stride = kw.get("stride", c["stride"])
+    R = kw.get("R", c["R"])
+    weight = kw.get("phase_weight", O.W_BISPEC)
+    plan = Plan(Channel(W=sp.W, H=sp.H, N=c["N"], R=R, stride=stride, fc=CS.FC, taper=c["taper"],
+                        phase_weight=weight, max_frames=sp.F))
+    b = CS.burst("ragged")
+    g = CS.gpu_run(plan, b["frames"], b["stf_emp"])
+    o = O.reconstruct_burst(b["frames"], c["N"], stride, CS.FC, R, c["taper"], b["stf_emp"], weight)
+    assert plan.info["n_sub"] == len(o["subs"])
+    wv = CS.used_pairs(c["N"], R)
+    idx = plan.pair_index(wv)
+    for s in (0, len(o["subs"]) - 1):
+        assert CS.rel_l2(g["B"][s][idx], CS.oracle_B_used(o["sub"][s]["In"], wv)) < SPEC_TOL
+    v = o["valid"]
+    assert np.array_equal(g["valid"], v)
+    assert CS.rel_l2(g["out"][v], o["out"][v]) < IMG_TOL
