@@ -206,7 +206,7 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps):
     for c in range(3):
         t = eng.submit(c, frames[c].numpy(), outs[c][0].numpy(), d_over_r0=r0[c])
         eng.poll(t, -1)
-    n = max(12, 4 * steps)
+    n = max(30, 6 * steps)
     rate = 0.6 * capacity                      # offered load: 60 % of the measured capacity
     rng = np.random.default_rng(2017)
     arrive = np.cumsum(rng.exponential(1.0 / rate, n))
@@ -239,7 +239,8 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps):
     span = time.perf_counter() - t0
     eng.close()
     return {"offered_bursts_per_s": round(rate, 3), "achieved_bursts_per_s": round(n / span, 3),
-            "bursts": n, "channels": "TiO 2560x2160, G-band 2560x2160, H-alpha 1024x1024 (uniform mix)",
+            "arrival_span_s": round(float(arrive[-1]), 3), "makespan_s": round(span, 3),
+            "realised_arrival_rate": round(n / float(arrive[-1]), 3), "bursts": n, "channels": "TiO 2560x2160, G-band 2560x2160, H-alpha 1024x1024 (uniform mix)",
             "latency_ms_p50": round(1000 * float(np.percentile(lat, 50)), 1),
             "latency_ms_p99": round(1000 * float(np.percentile(lat, 99)), 1),
             "nvst_rate_bursts_per_s": 0.3,

@@ -58,14 +58,44 @@ __device__ __forceinline__ float2 reduce8(float2 (&s)[PH_ITEMS], int lane) {
     return r;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(sa), "l"(gmem));
+}
+
+// Shared memory: item partial sums of the ring, the phasor table, the item
+// records of the next ring and the point records of this and the next ring.
+struct PhaseSmem {
+    float2* part;   // [max_ring_items]
+    float2* zs;     // [hb]
+    int4* itm;      // [max_ring_items] items of ring r + 1
+    int4* prc;      // [2][max_ring_points] point records, by ring parity
+};
+__host__ __device__ inline size_t phase_layout(int hb_rows, int pitch, int mri, int mrp, size_t* o_zs,
+                                               size_t* o_itm, size_t* o_prc) {
+    size_t o = 0;
+    o += ((size_t)mri * sizeof(float2) + 15) & ~(size_t)15;
+    *o_zs = o;
+    o += ((size_t)hb_rows * pitch * sizeof(float2) + 15) & ~(size_t)15;
+    *o_itm = o;
+    o += (size_t)mri * sizeof(int4);
+    *o_prc = o;
+    o += (size_t)2 * mrp * sizeof(int4);
+    return o;
+}
+
 __global__ void __launch_bounds__(PH_THREADS, 2)
 k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         double2* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K, pitch = p.box_pitch;
     const size_t hb = (size_t)p.hb_rows * pitch;
-    float2* part = reinterpret_cast<float2*>(smem);                      // [max_ring_items]
-    float2* zs = reinterpret_cast<float2*>(smem) + ((p.max_ring_items + 1) & ~1);  // [hb]
+    size_t o_zs, o_itm, o_prc;
+    phase_layout(p.hb_rows, pitch, p.max_ring_items, p.max_ring_points, &o_zs, &o_itm, &o_prc);
+    PhaseSmem sm{reinterpret_cast<float2*>(smem), reinterpret_cast<float2*>(smem + o_zs),
+                 reinterpret_cast<int4*>(smem + o_itm), reinterpret_cast<int4*>(smem + o_prc)};
+    float2* part = sm.part;
+    float2* zs = sm.zs;
     const int sl = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     double2* zo = z + (size_t)sl * hb;
     for (int e = tid; e < (int)hb; e += PH_THREADS) zs[e] = make_float2(0.f, 0.f);
@@ -87,27 +117,36 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         zo[K - 1] = make_double2(ax.x, -ax.y);
         zo[pitch + K] = ay;
     }
-    __syncthreads();
 
     const bool unit = p.weight == SM_W_UNIT;
     const float2* Bs = B + (size_t)sl * p.n_tiles * TILE_PAIRS;
-    // A batch is up to PH_ITEMS items of one warp.  Each item comes from the
-    // plan as (w and offset origin as four signed bytes, B offset, mask of
-    // lanes whose (w, v) pair is read); the lane's B value is loaded at once.
-    // B does not depend on the phases, so the next ring's first batch is
-    // loaded before the ring's barriers.
+    // Stage the item and point records of ring q (< n_rings) into shared
+    // memory: items into itm, points into prc[q & 1].
+    auto stage = [&](int q) {
+        if (q < p.n_rings) {
+            const int i0 = p.ring_items[q], ni = p.ring_items[q + 1] - i0;
+            const int p0 = p.ring_start[q], np = p.ring_start[q + 1] - p0;
+            for (int e = tid; e < ni; e += PH_THREADS) cp_async16(sm.itm + e, p.items + i0 + e);
+            int4* pr = sm.prc + (q & 1) * p.max_ring_points;
+            for (int e = tid; e < np; e += PH_THREADS) cp_async16(pr + e, p.point_rec + p0 + e);
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+    // A batch is up to PH_ITEMS items of one warp: per item the packed
+    // coordinates (w and the tile's offset origin as signed bytes) and this
+    // lane's B value (when the lane's (w, v) pair is read).
     float2 bv[PH_ITEMS];
     unsigned pk[PH_ITEMS];
     unsigned okm = 0;
-    auto load_batch = [&](int base, int i1) {
+    auto load_batch = [&](const int4* recs, int base, int ni) {
         okm = 0;
 #pragma unroll
         for (int q = 0; q < PH_ITEMS; ++q) {
-            const int it = base + q * PH_WARPS;
+            const int e = base + q * PH_WARPS;
             bv[q] = make_float2(0.f, 0.f);
             pk[q] = 0;
-            if (it < i1) {
-                const int4 item = p.items[it];
+            if (e < ni) {
+                const int4 item = recs[e];
                 pk[q] = (unsigned)item.x;
                 if ((unsigned)item.z & (1u << lane)) {
                     okm |= 1u << q;
@@ -116,12 +155,25 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
             }
         }
     };
-    load_batch(p.ring_items[0] + warp, p.ring_items[1]);
+    // Per ring r: (0) stage ring r+1's records; (1) items of ring r -> one
+    // FP32 partial per item; barrier; (2) load ring r+1's first batch from the
+    // staged records (its B loads overlap step 3); (3) one warp per point sums
+    // its items and stores z = S / |S|; barrier.
+    int i0 = p.ring_items[0], ni = p.ring_items[1] - i0, np = p.ring_start[1] - p.ring_start[0];
+    stage(0);
+    asm volatile("cp.async.wait_group 0;");
+    __syncthreads();                              // anchors and ring 0 records visible
+    load_batch(sm.itm, warp, ni);
+    __syncthreads();                              // staging buffer free again
     for (int r = 0; r < p.n_rings; ++r) {
-        const int i0 = p.ring_items[r], i1 = p.ring_items[r + 1];
+        const bool more = r + 1 < p.n_rings;
+        const int i0n = more ? p.ring_items[r + 1] : 0;
+        const int nin = more ? p.ring_items[r + 2] - i0n : 0;
+        const int npn = more ? p.ring_start[r + 2] - p.ring_start[r + 1] : 0;
+        stage(r + 1);
         // (1) items: FP32 products, one term per lane, FP32 item sums
-        for (int base = i0 + warp; base < i1; base += PH_WARPS * PH_ITEMS) {
-            if (base != i0 + warp) load_batch(base, i1);
+        for (int base = warp; base < ni; base += PH_WARPS * PH_ITEMS) {
+            if (base != warp) load_batch(p.items + i0, base, ni);
             float2 t[PH_ITEMS];
 #pragma unroll
             for (int q = 0; q < PH_ITEMS; ++q) {
@@ -149,21 +201,22 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
                 }
             }
             const float2 sum = reduce8(t, lane);
-            const int q = lane >> 2, it = base + q * PH_WARPS;
-            if ((lane & 3) == 0 && it < i1) part[it - i0] = sum;
+            const int e = base + (lane >> 2) * PH_WARPS;
+            if ((lane & 3) == 0 && e < ni) part[e] = sum;
         }
-        if (r + 1 < p.n_rings) load_batch(i1 + warp, p.ring_items[r + 2]);
-        __syncthreads();
-        // (2) one warp per point: sum of its items along a fixed shuffle
+        asm volatile("cp.async.wait_group 0;");
+        __syncthreads();                          // partials complete, ring r+1 records visible
+        if (more) load_batch(sm.itm, warp, nin);
+        // (3) one warp per point: sum of its items along a fixed shuffle
         // tree, then z = S / |S|.  FP32: the phasors feed the next rings in
         // FP32 anyway, and GB300's shared FP64 unit serialised this step
         // across warps when it ran in FP64.  The stored state is FP64.
-        const int pe = p.ring_start[r + 1];
-        for (int pt = p.ring_start[r] + warp; pt < pe; pt += PH_WARPS) {
-            const int a0 = p.point_items[pt], a1 = p.point_items[pt + 1];
+        const int4* pr = sm.prc + (r & 1) * p.max_ring_points;
+        for (int pl = warp; pl < np; pl += PH_WARPS) {
+            const int4 rec = pr[pl];
             float sx = 0.f, sy = 0.f;
-            for (int a = a0 + lane; a < a1; a += 32) {
-                const float2 v = part[a - i0];
+            for (int a = rec.z + lane; a < rec.w; a += 32) {
+                const float2 v = part[a];
                 sx += v.x;
                 sy += v.y;
             }
@@ -173,23 +226,25 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
             }
             if (lane == 0) {
-                const int2 w = p.points[pt];
                 const float n2 = sx * sx + sy * sy;
                 float2 zz = make_float2(1.f, 0.f);
                 if (n2 > 0.f) {
                     const float inv = rsqrtf(n2);
                     zz = make_float2(sx * inv, sy * inv);
                 }
-                const int o = w.y * pitch + w.x + K;
+                const int o = rec.y * pitch + rec.x + K;
                 zs[o] = zz;
                 zo[o] = make_double2((double)zz.x, (double)zz.y);
-                if (w.y == 0) {
-                    zs[-w.x + K] = make_float2(zz.x, -zz.y);
-                    zo[-w.x + K] = make_double2((double)zz.x, -(double)zz.y);
+                if (rec.y == 0) {
+                    zs[-rec.x + K] = make_float2(zz.x, -zz.y);
+                    zo[-rec.x + K] = make_double2((double)zz.x, -(double)zz.y);
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();                          // phasors visible, staging buffers free
+        i0 = i0n;
+        ni = nin;
+        np = npn;
     }
 }
 
@@ -197,13 +252,14 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
 
 namespace smk {
 
-size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items) {
-    return (size_t)((max_ring_items + 1) & ~1) * sizeof(float2) + (size_t)hb_rows * box_pitch * sizeof(float2);
+size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_ring_points) {
+    size_t a, b, c;
+    return phase_layout(hb_rows, box_pitch, max_ring_items, max_ring_points, &a, &b, &c);
 }
 
 cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M,
                          double2* z, cudaStream_t st) {
-    const size_t sm = phase_smem_bytes(p.hb_rows, p.box_pitch, p.max_ring_items);
+    const size_t sm = phase_smem_bytes(p.hb_rows, p.box_pitch, p.max_ring_items, p.max_ring_points);
     cudaError_t e = cudaFuncSetAttribute(k_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_phase<<<nsub, PH_THREADS, sm, st>>>(p, B, M, z);

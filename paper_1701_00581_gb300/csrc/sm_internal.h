@@ -53,7 +53,9 @@ struct PlanDev {
                                 //   within the subfield, mask of lanes whose pair is read
     const int* ring_items;      // [n_rings + 1] first item of each ring
     const int* point_items;     // [n_points + 1] first item of each point
-    int n_items, max_ring_items;
+    const int4* point_rec;      // [n_points] (wx, wy, first item, end item), items counted
+                                //   from the first item of the point's ring
+    int n_items, max_ring_items, max_ring_points;
     const double* t0;        // [hb_rows][box_pitch] diffraction OTF on the half box
 };
 
@@ -78,5 +80,5 @@ cudaError_t launch_inverse(const smi::PlanDev& p, int F, int sub0, int nsub, con
 cudaError_t launch_mosaic(const smi::PlanDev& p, const float* rec, float* out, uint8_t* valid,
                           cudaStream_t st);
 size_t spectra_smem_bytes(int N, int K);
-size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items);
+size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_ring_points);
 }  // namespace smk

@@ -73,7 +73,7 @@ int validate_channel(const sm_channel* ch) {
         set_error("fc*N too large for the shared-memory FFT at this N"); return SM_EINVAL;
     }
     const int pitch = ((2 * K + 1) + 3) / 4 * 4;
-    if (smk::phase_smem_bytes(K + 1, pitch, 0) > 200 * 1024) {
+    if (smk::phase_smem_bytes(K + 1, pitch, 0, 0) > 200 * 1024) {
         set_error("phase table exceeds shared memory"); return SM_EINVAL;
     }
     return SM_OK;
@@ -260,7 +260,15 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         if (rr > 0) d.max_ring_items = std::max(d.max_ring_items, pl->ring_items[rr] - pl->ring_items[rr - 1]);
     }
     d.n_items = (int)pl->items.size();
-    if (smk::phase_smem_bytes(d.hb_rows, d.box_pitch, d.max_ring_items) > 227 * 1024) {
+    d.max_ring_points = 0;
+    pl->point_rec.resize(d.n_points);
+    for (int rr = 0; rr < d.n_rings; ++rr) {
+        d.max_ring_points = std::max(d.max_ring_points, pl->ring_start[rr + 1] - pl->ring_start[rr]);
+        for (int pi = pl->ring_start[rr]; pi < pl->ring_start[rr + 1]; ++pi)
+            pl->point_rec[pi] = make_int4(pts[pi].x, pts[pi].y, pl->point_items[pi] - pl->ring_items[rr],
+                                          pl->point_items[pi + 1] - pl->ring_items[rr]);
+    }
+    if (smk::phase_smem_bytes(d.hb_rows, d.box_pitch, d.max_ring_items, d.max_ring_points) > 227 * 1024) {
         delete pl;
         set_error("phase recursion tables exceed shared memory");
         return SM_EINVAL;
@@ -284,6 +292,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         {pl->ring_items.data(), pl->ring_items.size() * sizeof(int), 0},
         {pl->point_items.data(), pl->point_items.size() * sizeof(int), 0},
         {winft.data(), winft.size() * sizeof(float2), 0},
+        {pl->point_rec.data(), pl->point_rec.size() * sizeof(int4), 0},
     };
     size_t total = 0;
     for (auto& p : pcs) { p.off = total; total += align256(std::max<size_t>(p.bytes, 1)); }
@@ -312,6 +321,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.ring_items = (const int*)at(12);
     d.point_items = (const int*)at(13);
     d.winft = (const float2*)at(14);
+    d.point_rec = (const int4*)at(15);
     *out = pl;
     return SM_OK;
 }

@@ -19,6 +19,7 @@ struct sm_plan {
     std::vector<int2> points;
     std::vector<int4> items;
     std::vector<int> ring_items, point_items;
+    std::vector<int4> point_rec;
     long long n_pairs = 0;
     int n_U = 0, n_V = 0;
     void* dmem = nullptr;            // device copy of every table
