@@ -11,13 +11,21 @@
 // (vx0 + kk, vy0 + q), kk = 0..7: 32 complex accumulators in registers for
 // the whole burst.  Per frame the CTA stages three rectangles of the frame
 // spectrum in shared memory: the targets W (8 x 16), the offsets V (4 x 8)
-// and U = W - V (11 x 23).  For its 32 pairs a thread reads 4 values of W,
-// 8 broadcast values of V and an 11-wide sliding window of U (12 shared
-// loads of 16 bytes for 32 pairs), so each triple product costs 8 FP32
-// FMA-pipe instructions.  FP32 spectra are staged by cp.async, four frames
-// per barrier, while the previous four frames are multiplied out.  A warp skips the offset columns (and so
-// whole tiles) in which none of its lanes owns a used pair.  Accumulators are
-// written once per burst.
+// and U = W - V (11 x 23, staged 24 wide).  For its 32 pairs a thread reads
+// 4 values of W, 8 broadcast values of V and an 11-wide sliding window of U
+// (12 shared loads of 16 bytes for 32 pairs), so each triple product costs
+// 8 FP32 FMA-pipe instructions.
+//
+// FP32 spectra are staged by cp.async, four frames per barrier, while the
+// previous four frames are multiplied out.  W and U start at even box
+// columns (the plan places the offset grid so that they do), so they move in
+// 16-byte copies of two spectrum values, and so does V when the box's
+// centre column K is odd: 212 copies per frame, two per thread (otherwise V
+// takes 32 8-byte copies).  A last, partial stage is padded with zero-filled
+// frames, which add nothing to the sums.  A warp skips the offset columns
+// (and so whole tiles) in which none of its lanes owns a used pair; warps
+// that own a used pair in every column run a copy of the frame loop without
+// the column tests.  Accumulators are written once per burst.
 #include "sm_internal.h"
 
 namespace {
@@ -35,11 +43,26 @@ constexpr int OFF_W = 0;
 constexpr int OFF_V = smi::WBY * PW;                      // 144
 constexpr int OFF_U = OFF_V + smi::VBY * smi::VBX;        // 176
 constexpr int BUF = OFF_U + UR * PU;                      // 462 float2 per frame buffer
-constexpr int NLOAD = smi::WBY * smi::WBX + smi::VBY * smi::VBX + UR * UC;  // 413
+constexpr int NLOAD = smi::WBY * smi::WBX + smi::VBY * smi::VBX + UR * UC;  // 413 values
 constexpr int THREADS = smi::BISPEC_THREADS;
-constexpr int LPT = (NLOAD + THREADS - 1) / THREADS;      // 4 elements per thread
+constexpr int LPT = (NLOAD + THREADS - 1) / THREADS;      // 4 values per thread (half precision)
 static_assert(OFF_V % 2 == 0 && OFF_U % 2 == 0 && BUF % 2 == 0 && PW % 2 == 0 && PU % 2 == 0,
-              "16-byte shared loads need even float2 offsets");
+              "16-byte shared accesses need even float2 offsets");
+
+// 16-byte staging of FP32 spectra: W as 8 rows x 8 chunks, U as 11 rows x 12
+// chunks (24 columns; the 24th is read by no used pair) and, with VCH, V as
+// 4 rows x 4 chunks; chunk c of W|V|U (VCH) or W|U goes to copy slot c / 128
+// of thread c % 128.  Without VCH, slot 1 of warp 0 copies V value `lane`
+// (8 bytes) and W|U chunks 128.. go to threads 32.., so the copy width is
+// uniform across each warp.
+constexpr int UCH = (UC + 1) / 2;                         // 12 chunks per U row
+constexpr int NCH_W = smi::WBY * smi::WBX / 2;            // 64
+constexpr int NCH_V = smi::VBY * smi::VBX / 2;            // 16
+constexpr int NCH_U = UR * UCH;                           // 132
+constexpr int NV = smi::VBY * smi::VBX;                   // 32
+static_assert(NCH_W + NCH_V + NCH_U <= 2 * THREADS && NCH_W + NCH_U <= 2 * THREADS - NV && NV == 32,
+              "two copy slots per thread");
+static_assert(smi::WBX % 2 == 0, "targets start at even box columns");
 
 // Bank check (16-byte loads, 8-lane phases): lanes 0..7 hold wyl = 0, 1 and
 // gx = 0..3.  Targets: 16-byte slot 9 wyl + 2 gx (+ j/2) -> {0,2,4,6} + {0,1}
@@ -67,12 +90,18 @@ __device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2
     return inH && w2 >= 2 && w2 <= r2i && v2 > 0 && v2 <= R2 && v2 < w2 && u2 < w2;
 }
 
-// 8-byte asynchronous copy global -> shared; bytes = 0 zero-fills.
+// Asynchronous copies global -> shared of 8 or 16 bytes; the first `bytes`
+// bytes come from global memory, the rest of the copy is zero-filled.
 __device__ __forceinline__ void cp_async8(unsigned smem_addr, const void* gmem, int bytes) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(smem_addr), "l"(gmem), "r"(bytes));
 }
+__device__ __forceinline__ void cp_async16(unsigned smem_addr, const void* gmem, int bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" :: "r"(smem_addr), "l"(gmem), "r"(bytes));
+}
 
-// One frame of the thread's 4 x 8 pairs from the staged rectangles.
+// One frame of the thread's 4 x 8 pairs from the staged rectangles.  FULL:
+// the warp owns a used pair in every offset column, so no column is tested.
+template <bool FULL>
 __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, int wyl, int gx, int warp,
                                                  unsigned kkmask, float2 (&acc)[4][smi::VBX]) {
     const float4* w4 = reinterpret_cast<const float4*>(Sb + OFF_W + wyl * PW + 4 * gx);
@@ -90,12 +119,12 @@ __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, 
     const float4* v4 = reinterpret_cast<const float4*>(Sb + OFF_V + warp * smi::VBX);
 #pragma unroll
     for (int k2 = 0; k2 < smi::VBX / 2; ++k2) {
-        if (!(kkmask & (3u << (2 * k2)))) continue;   // warp-uniform
-        const float4 bb = v4[k2];                       // I(v) for kk = 2 k2, 2 k2 + 1 (broadcast)
+        if (!FULL && !(kkmask & (3u << (2 * k2)))) continue;   // warp-uniform
+        const float4 bb = v4[k2];                               // I(v) for kk = 2 k2, 2 k2 + 1 (broadcast)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int kk = 2 * k2 + e;
-            if (!(kkmask & (1u << kk))) continue;       // warp-uniform
+            if (!FULL && !(kkmask & (1u << kk))) continue;      // warp-uniform
             const float2 b = e == 0 ? make_float2(bb.x, bb.y) : make_float2(bb.z, bb.w);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -118,7 +147,38 @@ template <> struct Staging<SM_FP32> { static constexpr bool ASYNC = true;  stati
 template <> struct Staging<SM_FP16> { static constexpr bool ASYNC = false; static constexpr int FB = 1; };
 template <> struct Staging<SM_BF16> { static constexpr bool ASYNC = false; static constexpr int FB = 1; };
 
-template <int PREC>
+// Box index of spectrum value (kx, ky), or -1 outside the stored box.
+__device__ __forceinline__ int box_index(const PlanDev& p, int kx, int ky) {
+    const bool in = ky >= -p.R && ky <= p.K && kx >= -p.K && kx <= p.K;
+    return in ? (ky + p.R) * p.box_pitch + (kx + p.K) : -1;
+}
+
+// Source, destination and size of chunk c of W|V|U (VCH) or W|U of a tile:
+// two spectrum values from an even box column, both, the first or neither
+// inside the box (the box's last column 2K is even, so a chunk never starts
+// outside it and ends inside).
+template <bool VCH>
+__device__ __forceinline__ void chunk_copy(const PlanDev& p, int c, int wx0, int wy0, int vx0, int vy0,
+                                           int& src, int& dst, int& bytes) {
+    int kx, ky;
+    if (c < NCH_W) {
+        const int r = c >> 3, h = c & 7;
+        kx = wx0 + 2 * h; ky = wy0 + r; dst = OFF_W + r * PW + 2 * h;
+    } else if (VCH && c < NCH_W + NCH_V) {
+        const int c2 = c - NCH_W, r = c2 >> 2, h = c2 & 3;
+        kx = vx0 + 2 * h; ky = vy0 + r; dst = OFF_V + r * smi::VBX + 2 * h;
+    } else {
+        const int c2 = c - NCH_W - (VCH ? NCH_V : 0), r = c2 / UCH, h = c2 - r * UCH;
+        kx = wx0 - vx0 - (smi::VBX - 1) + 2 * h; ky = wy0 - vy0 - (smi::VBY - 1) + r;
+        dst = OFF_U + r * PU + 2 * h;
+    }
+    const int i0 = box_index(p, kx, ky), i1 = box_index(p, kx + 1, ky);
+    src = i0 >= 0 ? i0 : 0;
+    bytes = i0 < 0 ? 0 : (i1 >= 0 ? 16 : 8);
+}
+
+// VCH: V moves in 16-byte chunks (every tile's vx0 + K is even).
+template <int PREC, bool VCH>
 __global__ void __launch_bounds__(THREADS, 4)
 k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict__ B) {
     constexpr bool ASYNC = Staging<PREC>::ASYNC;
@@ -129,30 +189,6 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
     const int wx0 = T.x, wy0 = T.y, vx0 = T.z, vy0 = T.w;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int wyl = lane >> 2, gx = lane & 3;
-
-    // Which spectrum element each thread stages, and where it goes.
-    int src[LPT], dst[LPT];
-#pragma unroll
-    for (int i = 0; i < LPT; ++i) {
-        const int e = tid + i * THREADS;
-        int kx = 0, ky = 0, d = -1;
-        if (e < smi::WBY * smi::WBX) {
-            const int r = e / smi::WBX, c = e - r * smi::WBX;
-            kx = wx0 + c; ky = wy0 + r; d = OFF_W + r * PW + c;
-        } else if (e < smi::WBY * smi::WBX + smi::VBY * smi::VBX) {
-            const int e2 = e - smi::WBY * smi::WBX;
-            const int r = e2 / smi::VBX, c = e2 - r * smi::VBX;
-            kx = vx0 + c; ky = vy0 + r; d = OFF_V + r * smi::VBX + c;
-        } else if (e < NLOAD) {
-            const int e2 = e - smi::WBY * smi::WBX - smi::VBY * smi::VBX;
-            const int r = e2 / UC, c = e2 - r * UC;
-            kx = wx0 - vx0 - (smi::VBX - 1) + c; ky = wy0 - vy0 - (smi::VBY - 1) + r;
-            d = OFF_U + r * PU + c;
-        }
-        dst[i] = d;
-        const bool inbox = d >= 0 && ky >= -p.R && ky <= p.K && kx >= -p.K && kx <= p.K;
-        src[i] = inbox ? (ky + p.R) * p.box_pitch + (kx + p.K) : -1;
-    }
 
     // Offset columns kk for which some lane of this warp owns a used pair:
     // a warp-uniform mask, so the warp skips columns (and whole tiles) it
@@ -179,28 +215,46 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
     if (ASYNC) {
         const float2* sp = reinterpret_cast<const float2*>(spec) + sbase;
         const int nst = (F + FB - 1) / FB;
-        // per element: global source (frame 0), shared destination (buffer 0)
-        // and copy size (0 = zero fill outside the box), fixed for the CTA
-        const float2* gsrc[LPT];
-        unsigned sdst[LPT];
-        int nb[LPT];
-#pragma unroll
-        for (int i = 0; i < LPT; ++i) {
-            gsrc[i] = sp + (src[i] >= 0 ? src[i] : 0);
-            sdst[i] = (unsigned)__cvta_generic_to_shared(S + (dst[i] >= 0 ? dst[i] : 0));
-            nb[i] = src[i] >= 0 ? 8 : 0;
+        // Copy slots, fixed for the CTA: global source at frame 0, shared
+        // destination in buffer 0 and size.
+        int src, dst, nb0, nb1 = 0;
+        chunk_copy<VCH>(p, tid, wx0, wy0, vx0, vy0, src, dst, nb0);
+        const float2* g0 = sp + src;
+        const unsigned s0 = (unsigned)__cvta_generic_to_shared(S + dst);
+        const bool v8 = !VCH && warp == 0;                  // warp 0 copies V by 8 bytes
+        const int c1 = VCH ? tid + THREADS : tid + THREADS - NV;
+        const bool has1 = v8 || c1 < NCH_W + NCH_U + (VCH ? NCH_V : 0);
+        if (v8) {
+            const int r = lane >> 3, c = lane & 7;
+            const int i = box_index(p, vx0 + c, vy0 + r);
+            src = i >= 0 ? i : 0; dst = OFF_V + r * smi::VBX + c; nb1 = i >= 0 ? 8 : 0;
+        } else if (has1) {
+            chunk_copy<VCH>(p, c1, wx0, wy0, vx0, vy0, src, dst, nb1);
+        } else {
+            src = 0; dst = 0;
         }
+        const float2* g1 = sp + src;
+        const unsigned s1 = (unsigned)__cvta_generic_to_shared(S + dst);
+        auto copy = [&](unsigned soff, size_t goff, int n0, int n1) {
+            cp_async16(s0 + soff, g0 + goff, n0);
+            if (v8) cp_async8(s1 + soff, g1 + goff, n1);
+            else if (has1) cp_async16(s1 + soff, g1 + goff, n1);
+        };
+        // Stage st holds frames FB st .. FB st + FB - 1; frames past F are
+        // zero-filled (no global read) so that every stage is multiplied out whole.
         auto issue = [&](int st) {
             if (st < nst) {
+                const unsigned sb = (unsigned)((st & 1) * FB * BUF * sizeof(float2));
+                if (st * FB + FB <= F) {
 #pragma unroll
-                for (int ff = 0; ff < FB; ++ff) {
-                    const int f = st * FB + ff;
-                    if (f < F) {
-                        const unsigned soff = (unsigned)(((st & 1) * FB + ff) * BUF * sizeof(float2));
-                        const size_t goff = (size_t)f * box;
+                    for (int ff = 0; ff < FB; ++ff)
+                        copy(sb + ff * BUF * sizeof(float2), (size_t)(st * FB + ff) * box, nb0, nb1);
+                } else {
 #pragma unroll
-                        for (int i = 0; i < LPT; ++i)
-                            if (dst[i] >= 0) cp_async8(sdst[i] + soff, gsrc[i] + goff, nb[i]);
+                    for (int ff = 0; ff < FB; ++ff) {
+                        const bool in = st * FB + ff < F;
+                        copy(sb + ff * BUF * sizeof(float2), in ? (size_t)(st * FB + ff) * box : 0,
+                             in ? nb0 : 0, in ? nb1 : 0);
                     }
                 }
             }
@@ -213,12 +267,38 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
             issue(st + 1);
             if (!active) continue;
             const float2* Sst = S + (st & 1) * FB * BUF;
+            if (kkmask == 0xffu) {
 #pragma unroll
-            for (int ff = 0; ff < FB; ++ff)
-                if (st * FB + ff < F) accumulate_frame(Sst + ff * BUF, wyl, gx, warp, kkmask, acc);
+                for (int ff = 0; ff < FB; ++ff) accumulate_frame<true>(Sst + ff * BUF, wyl, gx, warp, kkmask, acc);
+            } else {
+#pragma unroll 1
+                for (int ff = 0; ff < FB; ++ff) accumulate_frame<false>(Sst + ff * BUF, wyl, gx, warp, kkmask, acc);
+            }
         }
         asm volatile("cp.async.wait_group 0;");
     } else {
+        // Which spectrum value each thread stages, and where it goes.
+        int src[LPT], dst[LPT];
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) {
+            const int e = tid + i * THREADS;
+            int d = -1, s = -1;
+            if (e < smi::WBY * smi::WBX) {
+                const int r = e / smi::WBX, c = e - r * smi::WBX;
+                s = box_index(p, wx0 + c, wy0 + r); d = OFF_W + r * PW + c;
+            } else if (e < smi::WBY * smi::WBX + smi::VBY * smi::VBX) {
+                const int e2 = e - smi::WBY * smi::WBX;
+                const int r = e2 / smi::VBX, c = e2 - r * smi::VBX;
+                s = box_index(p, vx0 + c, vy0 + r); d = OFF_V + r * smi::VBX + c;
+            } else if (e < NLOAD) {
+                const int e2 = e - smi::WBY * smi::WBX - smi::VBY * smi::VBX;
+                const int r = e2 / UC, c = e2 - r * UC;
+                s = box_index(p, wx0 - vx0 - (smi::VBX - 1) + c, wy0 - vy0 - (smi::VBY - 1) + r);
+                d = OFF_U + r * PU + c;
+            }
+            dst[i] = d;
+            src[i] = s;
+        }
         float2 pre[LPT];
 #pragma unroll
         for (int i = 0; i < LPT; ++i)
@@ -235,7 +315,7 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
                 for (int i = 0; i < LPT; ++i)
                     pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, fb + src[i]) : make_float2(0.f, 0.f);
             }
-            if (active) accumulate_frame(Sb, wyl, gx, warp, kkmask, acc);
+            if (active) accumulate_frame<false>(Sb, wyl, gx, warp, kkmask, acc);
         }
     }
 
@@ -260,9 +340,15 @@ namespace smk {
 cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, int nsub, float2* B,
                               cudaStream_t st) {
     dim3 grid(p.n_tiles, nsub);
-    if (p.prec == SM_FP32) k_bispectrum<SM_FP32><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-    else if (p.prec == SM_FP16) k_bispectrum<SM_FP16><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-    else k_bispectrum<SM_BF16><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+    const bool vch = ((p.v_org + p.K) & 1) == 0;     // every tile's V starts at an even column
+    if (p.prec == SM_FP32) {
+        if (vch) k_bispectrum<SM_FP32, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        else k_bispectrum<SM_FP32, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+    } else if (p.prec == SM_FP16) {
+        k_bispectrum<SM_FP16, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+    } else {
+        k_bispectrum<SM_BF16, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+    }
     return cudaGetLastError();
 }
 

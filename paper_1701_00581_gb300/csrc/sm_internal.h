@@ -35,6 +35,8 @@ struct PlanDev {
     int r2i;                 // floor((fc N)^2): |k|^2 <= r2i  <=>  |k| <= fc N
     int n_tiles, n_rings, n_points;
     int n_wbx, n_wby;
+    int v_org;               // x origin of the offset-block grid (odd: -R, or -R - 7 for even R),
+                             //   so that every difference rectangle starts at an even box column
     int prec, weight;
     const int4* subs;        // [n_sub] x0, y0, w, h
     const float* winx;       // [n_sub][N] window along x (0 beyond the extent)

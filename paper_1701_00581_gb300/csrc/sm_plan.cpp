@@ -167,7 +167,13 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     // bispectrum tiles: every (w-block, v-block) holding a used pair
     d.n_wbx = (2 * K + 1 + WBX - 1) / WBX;
     d.n_wby = (K + 1 + WBY - 1) / WBY;
-    pl->n_vbx = (2 * R + 1 + VBX - 1) / VBX;
+    // The difference rectangle of a tile starts at box column
+    // wx0 - vx0 - (VBX - 1) + K = WBX wbx - vx0 - (VBX - 1); an odd vx0 makes it even
+    // (VBX - 1 is odd), so the bispectrum kernel can stage it in 16-byte copies.
+    // For even R the grid ends at column R (origin -R - (VBX - 1)), for odd R it
+    // starts at -R: either way no block reaches past the offset disk on one side.
+    d.v_org = (R % 2 == 0) ? -R - (VBX - 1) : -R;
+    pl->n_vbx = (R - d.v_org + 1 + VBX - 1) / VBX;
     pl->n_vby = (2 * R + 1 + VBY - 1) / VBY;
     const int nwb = d.n_wbx * d.n_wby, nvb = pl->n_vbx * pl->n_vby;
     pl->tile_of.assign((size_t)nwb * nvb, -1);
@@ -179,7 +185,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
             const int wx0 = -K + WBX * wbx, wy0 = WBY * wby;
             for (int vby = 0; vby < pl->n_vby; ++vby)
                 for (int vbx = 0; vbx < pl->n_vbx; ++vbx) {
-                    const int vx0 = -R + VBX * vbx, vy0 = -R + VBY * vby;
+                    const int vx0 = d.v_org + VBX * vbx, vy0 = -R + VBY * vby;
                     long long cnt = 0;
                     for (int a = 0; a < WBY; ++a)
                         for (int b = 0; b < WBX; ++b)
@@ -194,6 +200,12 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
                 }
         }
     d.n_tiles = (int)pl->tiles.size();
+    // The bispectrum kernel stages W and U = W - V in 16-byte copies from even
+    // box columns of an even-pitched box.
+    for (const int4& T : pl->tiles)
+        if (((T.x + K) & 1) || ((T.x - T.z - (VBX - 1) + K) & 1) || (d.box_pitch & 1)) {
+            set_error("internal: bispectrum tile not on an even box column"); return SM_EINVAL;
+        }
     pl->n_pairs = npairs;
     pl->wb_start.assign(nwb + 1, 0);
     for (int b = 0; b < nwb; ++b) pl->wb_start[b + 1] = pl->wb_start[b] + wb_count[b];
@@ -369,11 +381,11 @@ extern "C" int sm_plan_pair_index(const sm_plan* plan, long long n, const int* w
         idx[i] = -1;
         if (!pair_used_host(wx, wy, vx, vy, d.r2i, R * R)) continue;
         const int wbx = (wx + K) / WBX, wby = wy / WBY;
-        const int vbx = (vx + R) / VBX, vby = (vy + R) / VBY;
+        const int vbx = (vx - d.v_org) / VBX, vby = (vy + R) / VBY;
         const int t = plan->tile_of[(size_t)(wby * d.n_wbx + wbx) * nvb + vby * plan->n_vbx + vbx];
         if (t < 0) continue;
         const int wl = (wy - wby * WBY) * WBX + (wx + K - wbx * WBX);
-        const int vl = (vy + R - vby * VBY) * VBX + (vx + R - vbx * VBX);
+        const int vl = (vy + R - vby * VBY) * VBX + (vx - d.v_org - vbx * VBX);
         idx[i] = (long long)t * TILE_PAIRS + (long long)wl * TILE_V + vl;
     }
     return SM_OK;

@@ -251,3 +251,27 @@ def test_method_variants_match_oracle(torch, name, kw):
     v = o["valid"]
     assert np.array_equal(g["valid"], v)
     assert CS.rel_l2(g["out"][v], o["out"][v]) < IMG_TOL
+
+
+def test_odd_R_at_256_matches_oracle(torch):
+    """N = 256 with an odd offset radius (R = 9): the offset-block grid then
+    starts at -R and the offsets move in 16-byte chunks (the box centre
+    column K = 73 is odd), unlike the even-R and N = 64 cases above.  Two
+    subfields, the second ragged (172 px wide), 4 uint16 frames."""
+    from paper_1701_00581_gb300 import Channel, Plan
+    from synth import burst as S
+    spec = S.BurstSpec(W=300, H=256, F=4, N=256, dr0=(5.0, 9.0), counts=True)
+    b = S.make_burst(spec, channel=11, burst=0)
+    N, R, stride, taper = 256, 9, 128, 16
+    plan = Plan(Channel(W=spec.W, H=spec.H, N=N, R=R, stride=stride, fc=CS.FC, taper=taper, max_frames=spec.F))
+    g = CS.gpu_run(plan, b["frames"], b["stf_emp"])
+    o = O.reconstruct_burst(b["frames"], N, stride, CS.FC, R, taper, b["stf_emp"])
+    assert plan.info["n_sub"] == len(o["subs"]) == 2
+    wv = CS.used_pairs(N, R)
+    idx = plan.pair_index(wv)
+    assert (idx >= 0).all()
+    for s in range(2):
+        assert CS.rel_l2(g["B"][s][idx], CS.oracle_B_used(o["sub"][s]["In"], wv)) < SPEC_TOL
+    v = o["valid"]
+    assert np.array_equal(g["valid"], v)
+    assert CS.rel_l2(g["out"][v], o["out"][v]) < IMG_TOL
