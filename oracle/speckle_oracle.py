@@ -23,6 +23,10 @@ stated in each docstring:
   mean power in the half-plane corners of the (2K+1)^2 box outside the disk;
 * bispectrum (Sect. 2, Sect. 3.2; Weigelt 1977) on the pair domain
   D = {u in upper half plane, |u| <= r, 0 < |v| <= R, |u+v| <= r};
+* seeing (Sect. 3.1; von der Luehe 1984): D/r0 of every non-overlapping
+  N x N cube by a least-squares fit of a model spectral ratio (Fried's
+  long-exposure OTF squared over the model STF) to the observed one, r0
+  averaged over the cubes;
 * modulus (Sect. 3.2, Eq. 1) with a model STF (Sect. 3.2), filtered by the
   diffraction OTF T0;
 * recursive phase (Sect. 3.2; LWW 1983), rings of equal |w|^2, anchors from
@@ -297,6 +301,136 @@ def amplitude(P: np.ndarray, noise: float, stf: np.ndarray, N: int, fc: float) -
 
 
 # ----------------------------------------------------------------------------
+# seeing (Sect. 3.1: spectral ratio technique, von der Luehe 1984)
+# ----------------------------------------------------------------------------
+
+SEEING_STOP = 0.05                 # fit annuli until the observed ratio first drops below this
+SEEING_GRID = (1.0, 64.0, 256)     # D/r0 candidates: log-spaced from, to, count
+
+
+def seeing_cubes(W: int, H: int, N: int, stride: int) -> List[int]:
+    """Indices of the subfields that form the seeing cubes (Sect. 3.1).
+
+    The burst is cut into non-overlapping N x N cubes from the image origin
+    (80 of 256^2 for a 2560 x 2160 TiO burst).  With a stride dividing N
+    these are exactly the full-size subfields whose corner lies on the N
+    grid, so their spectra are the subfields' own (same window).
+    """
+    subs = subfield_grid(W, H, N, stride)
+    return [i for i, (x0, y0, w, h) in enumerate(subs)
+            if x0 % N == 0 and y0 % N == 0 and w == N and h == N]
+
+
+def annulus_index(kx: np.ndarray, ky: np.ndarray) -> np.ndarray:
+    """Nearest integer radius b of |k| (annuli of unit width).
+
+    (2b - 1)^2 <= 4|k|^2 < (2b + 1)^2, evaluated in integers; |k| is never a
+    half-integer on the lattice, so there are no ties.
+    """
+    q4 = 4 * (np.asarray(kx, dtype=np.int64) ** 2 + np.asarray(ky, dtype=np.int64) ** 2)
+    s = np.array([math.isqrt(int(v)) for v in np.ravel(q4)], dtype=np.int64).reshape(np.shape(q4))
+    return (s + 1) // 2
+
+
+def spectral_ratio(P: np.ndarray, M: np.ndarray, noise: float, F: int, N: int,
+                   fc: float) -> Tuple[np.ndarray, np.ndarray]:
+    """Annulus sums of the spectral ratio |<I>|^2 / <|I|^2> (von der Luehe 1984).
+
+    Over the half-plane domain U n H, annulus b = 0..K+1:
+    num_b = sum (F |M|^2 - P) / (F - 1), the power of the mean spectrum with
+    the finite-average residual removed (E|M_F|^2 = |E M|^2 + (P - |E M|^2)/F),
+    and den_b = sum (P - noise), the speckle power above the noise floor.
+    Both readings (debiasing and noise subtraction) are ours; the paper only
+    names the technique.  P and M are on the centred N x N grid.
+    """
+    if F < 2:
+        raise ValueError("the spectral ratio needs at least two frames")
+    r = cutoff_radius(N, fc)
+    K = int(math.floor(r))
+    r2i = int(math.floor(r * r))
+    k = np.arange(-(N // 2), N - N // 2, dtype=np.int64)
+    KX, KY = np.meshgrid(k, k)
+    dom = in_half_plane(KX, KY) & (KX * KX + KY * KY <= r2i)
+    b = annulus_index(KX[dom], KY[dom])
+    m2 = (F * np.abs(M[dom]) ** 2 - P[dom]) / (F - 1)
+    num = np.zeros(K + 2)          # |k| <= r rounds to at most K + 1
+    den = np.zeros(K + 2)
+    for bi, a, c in zip(b, m2, P[dom] - noise):
+        num[bi] += a
+        den[bi] += c
+    return num, den
+
+
+def ratio_model(rho: np.ndarray, x: float, ck: float = 0.435) -> np.ndarray:
+    """Model spectral ratio |T_LE|^2 / STF at D/r0 = x, both normalised at 0.
+
+    Long-exposure transfer function T0 exp(-3.44 (rho x)^(5/3)) (Fried 1966)
+    squared over the model STF of ``stf_model`` (normalised to 1 at 0), at
+    rho = |k| / r < 1.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    T0 = (2.0 / np.pi) * (np.arccos(rho) - rho * np.sqrt(1.0 - rho * rho))
+    e = np.exp(-6.88 * (rho * x) ** (5.0 / 3.0))
+    return T0 * T0 * e * (1.0 + ck / (x * x)) / (T0 * T0 * e + ck * T0 / (x * x))
+
+
+def fit_d_over_r0(num: np.ndarray, den: np.ndarray, N: int, fc: float, ck: float = 0.435) -> float:
+    """D/r0 whose model ratio best matches the observed one (least squares).
+
+    Annuli b = 1, 2, ... are used until the first with den_b <= 0 or an
+    observed ratio num_b/den_b below SEEING_STOP (the informative part of the
+    curve, where it falls from 1 towards the noise).  The cost
+    J(x) = sum_b (num_b/den_b - ratio_model(b/r, x))^2 is evaluated on the
+    SEEING_GRID candidates; the first minimum is refined by a parabola through
+    it and its neighbours in log x (not at the ends of the grid).  With no
+    usable annulus the estimate is the largest candidate.
+    """
+    r = cutoff_radius(N, fc)
+    bins = []
+    for b in range(1, len(num)):
+        if not den[b] > 0.0 or num[b] / den[b] < SEEING_STOP:
+            break
+        bins.append(b)
+    lo, hi, n = SEEING_GRID
+    lx = np.log(lo) + (np.log(hi) - np.log(lo)) * np.arange(n) / (n - 1)
+    if not bins:
+        return float(hi)
+    bins = np.array(bins)
+    eps = num[bins] / den[bins]
+    rho = bins / r
+    J = np.array([np.sum((eps - ratio_model(rho, math.exp(v), ck)) ** 2) for v in lx])
+    i = int(np.argmin(J))
+    t = lx[i]
+    if 0 < i < n - 1:
+        curv = J[i - 1] - 2.0 * J[i] + J[i + 1]
+        if curv > 0.0:
+            h = lx[1] - lx[0]
+            t = lx[i] + 0.5 * h * (J[i - 1] - J[i + 1]) / curv
+    return float(math.exp(t))
+
+
+def estimate_seeing(frames: np.ndarray, N: int, stride: int, fc: float, taper: int,
+                    ck: float = 0.435) -> Tuple[np.ndarray, float]:
+    """Per-cube D/r0 and the burst's D over mean r0 (Sect. 3.1).
+
+    Each non-overlapping cube gives an estimate from its spectral ratio; the
+    estimates of r0 are averaged, so the burst value is 1 / mean(1 / x_c).
+    """
+    F, H, W = frames.shape
+    subs = subfield_grid(W, H, N, stride)
+    xs = []
+    for c in seeing_cubes(W, H, N, stride):
+        In, _, _ = frame_spectra(frames, subs[c], N, taper)
+        P, M = power_mean(In)
+        num, den = spectral_ratio(P, M, noise_floor(P, N, fc), F, N, fc)
+        xs.append(fit_d_over_r0(num, den, N, fc, ck))
+    if not xs:
+        raise ValueError("no seeing cube: the stride must divide N and the image hold one N x N cube")
+    xs = np.array(xs)
+    return xs, float(1.0 / np.mean(1.0 / xs))
+
+
+# ----------------------------------------------------------------------------
 # recursive phase (Sect. 3.2: speckle masking phase, LWW 1983)
 # ----------------------------------------------------------------------------
 class _PairIndex:
@@ -463,10 +597,18 @@ def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: 
 
 
 def reconstruct_burst(frames: np.ndarray, N: int, stride: int, fc: float, R: int, taper: int,
-                      stf: np.ndarray, weight: int = W_BISPEC,
-                      subfields: Optional[Sequence[int]] = None) -> Dict:
-    """Whole burst: every subfield (or the listed ones), then the mosaic."""
+                      stf: Optional[np.ndarray], weight: int = W_BISPEC,
+                      subfields: Optional[Sequence[int]] = None, ck: float = 0.435) -> Dict:
+    """Whole burst: every subfield (or the listed ones), then the mosaic.
+
+    With ``stf`` None the STF is the model at the seeing estimated from the
+    burst itself (Sect. 3.1, ``estimate_seeing``), as the paper does.
+    """
     F, H, W = frames.shape
+    seeing = None
+    if stf is None:
+        seeing = estimate_seeing(frames, N, stride, fc, taper, ck)
+        stf = stf_model(N, fc, [seeing[1]], ck)
     subs = subfield_grid(W, H, N, stride)
     pairs = pair_domain(N, fc, R)
     pick = range(len(subs)) if subfields is None else subfields
@@ -475,4 +617,5 @@ def reconstruct_burst(frames: np.ndarray, N: int, stride: int, fc: float, R: int
     out = valid = None
     if subfields is None:
         out, valid = mosaic([results[s]["rec"] for s in range(len(subs))], subs, W, H, taper)
-    return {"subs": subs, "pairs": pairs, "sub": results, "out": out, "valid": valid}
+    return {"subs": subs, "pairs": pairs, "sub": results, "out": out, "valid": valid,
+            "seeing": seeing, "stf": stf}

@@ -339,3 +339,117 @@ def test_mosaic_undoes_the_window():
     assert np.all(out[~valid] == 0)
     # a pixel covered by exactly one tile near the corner with tiny weight is invalid
     assert not valid[0, 0]
+
+
+# ---------------------------------------------------------------------------
+# seeing (Sect. 3.1: spectral ratio technique, von der Luehe 1984)
+# ---------------------------------------------------------------------------
+
+def test_seeing_cubes_match_the_paper_count():
+    # Sect. 3.1: a 2560 x 2160 burst gives 80 non-overlapping 256^2 cubes
+    for stride in (64, 128, 256):
+        cubes = O.seeing_cubes(2560, 2160, 256, stride)
+        assert len(cubes) == 80
+        subs = O.subfield_grid(2560, 2160, 256, stride)
+        corners = sorted((subs[c][0], subs[c][1]) for c in cubes)
+        assert corners == sorted((x, y) for x in range(0, 2560 - 255, 256) for y in range(0, 2160 - 255, 256))
+    assert len(O.seeing_cubes(1024, 1024, 128, 64)) == 64
+    assert len(O.seeing_cubes(150, 110, 64, 32)) == 2          # one row of two; the rest is ragged
+    assert O.seeing_cubes(60, 60, 64, 32) == []
+
+
+def test_annulus_index_is_nearest_integer_radius():
+    k = np.arange(-80, 81)
+    KX, KY = np.meshgrid(k, k)
+    b = O.annulus_index(KX, KY)
+    assert np.array_equal(b, np.rint(np.hypot(KX, KY)).astype(np.int64))
+
+
+def test_spectral_ratio_of_identical_frames_is_one():
+    N = 64
+    rng = np.random.default_rng(3)
+    I = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    F = 7
+    In = np.repeat(I[None], F, axis=0)
+    P, M = O.power_mean(In)
+    num, den = O.spectral_ratio(P, M, 0.0, F, N, FC)
+    m = den > 0
+    K = int(math.floor(O.cutoff_radius(N, FC)))
+    assert m[1:K + 1].all()
+    assert np.allclose(num[m] / den[m], 1.0, rtol=1e-12, atol=0)
+
+
+def test_spectral_ratio_two_frames_is_cross_power():
+    # F = 2: (2 |(I1 + I2)/2|^2 - (|I1|^2 + |I2|^2)/2) / 1 = Re(I1 conj I2)
+    N = 32
+    rng = np.random.default_rng(4)
+    I1, I2 = (rng.standard_normal((2, N, N)) + 1j * rng.standard_normal((2, N, N)))
+    P, M = O.power_mean(np.stack([I1, I2]))
+    num, den = O.spectral_ratio(P, M, 0.25, 2, N, FC)
+    k = np.arange(-(N // 2), N - N // 2)
+    KX, KY = np.meshgrid(k, k)
+    r = O.cutoff_radius(N, FC)
+    dom = O.in_half_plane(KX, KY) & (KX * KX + KY * KY <= math.floor(r * r))
+    b = np.rint(np.hypot(KX, KY)).astype(int)
+    cross = (I1 * np.conj(I2)).real
+    for bi in range(len(num)):
+        sel = dom & (b == bi)
+        assert num[bi] == pytest.approx(cross[sel].sum(), rel=1e-12, abs=1e-12)
+        assert den[bi] == pytest.approx((P[sel] - 0.25).sum(), rel=1e-12, abs=1e-12)
+
+
+def test_ratio_model_limits_and_consistency_with_stf_model():
+    # rho -> 0 gives 1; on the grid it is |T_LE|^2 / STF with the pinned stf_model
+    assert O.ratio_model(np.array([1e-9]), 9.0)[0] == pytest.approx(1.0, abs=1e-9)
+    N, x = 128, 7.5
+    stf = O.stf_model(N, FC, [x])
+    T0 = O.otf_t0(N, FC)
+    r = O.cutoff_radius(N, FC)
+    k = np.arange(-(N // 2), N - N // 2)
+    rho = np.hypot(k[None, :], k[:, None]) / r
+    tle = T0 * np.exp(-3.44 * (rho * x) ** (5.0 / 3.0))            # Fried 1966 long exposure
+    m = (rho > 0) & (rho < 0.9)
+    assert np.allclose(O.ratio_model(rho[m], x), tle[m] ** 2 / stf[m], rtol=1e-12)
+    # worse seeing lowers the ratio at fixed frequency (rho x beyond the knee)
+    assert O.ratio_model(np.array([0.2]), 12.0)[0] < O.ratio_model(np.array([0.2]), 6.0)[0]
+
+
+@pytest.mark.parametrize("x_true", [3.0, 6.5, 11.0, 20.0])
+def test_fit_recovers_seeing_from_model_spectra(x_true):
+    # One object component per annulus, on the +kx axis at radius exactly b:
+    # P = |O|^2 STF(x), M = O T_LE(x), F huge (no finite-average residual);
+    # the observed ratio is then the model ratio at rho = b / r.
+    N = 256
+    r = O.cutoff_radius(N, FC)
+    K = int(math.floor(r))
+    stf = O.stf_model(N, FC, [x_true])
+    T0 = O.otf_t0(N, FC)
+    c = N // 2
+    P = np.zeros((N, N))
+    M = np.zeros((N, N), complex)
+    rng = np.random.default_rng(5)
+    for b in range(1, K + 1):
+        o = rng.uniform(0.5, 2.0) * np.exp(2j * np.pi * rng.uniform())
+        rho = b / r
+        P[c, c + b] = abs(o) ** 2 * stf[c, c + b]
+        M[c, c + b] = o * T0[c, c + b] * math.exp(-3.44 * (rho * x_true) ** (5.0 / 3.0))
+    num, den = O.spectral_ratio(P, M, 0.0, 10 ** 12, N, FC)
+    x = O.fit_d_over_r0(num, den, N, FC)
+    assert x == pytest.approx(x_true, rel=5e-3)
+
+
+def test_estimate_seeing_orders_bursts_by_seeing():
+    # Reported accuracy, loosely gated: the model STF is a reading, so the
+    # estimate is biased, but it must rank the seeing and stay near it.
+    import dataclasses
+    est = {}
+    for d in (5.0, 12.0):
+        spec = dataclasses.replace(S.CONFIGS["halpha1024"], W=256, H=128, F=40, dr0=(d, d))
+        b = S.make_burst(spec, channel=5, burst=int(d))
+        xs, xb = O.estimate_seeing(b["frames"], 128, 64, FC, 16)
+        assert len(xs) == 2
+        assert xb == pytest.approx(1.0 / np.mean(1.0 / xs))
+        est[d] = xb
+    assert est[5.0] < est[12.0]
+    for d, x in est.items():
+        assert d / 1.5 < x < d * 1.5
