@@ -377,9 +377,10 @@ def ratio_model(rho: np.ndarray, x: float, ck: float = 0.435) -> np.ndarray:
 def fit_d_over_r0(num: np.ndarray, den: np.ndarray, N: int, fc: float, ck: float = 0.435) -> float:
     """D/r0 whose model ratio best matches the observed one (least squares).
 
-    Annuli b = 1, 2, ... are used until the first with den_b <= 0 or an
-    observed ratio num_b/den_b below SEEING_STOP (the informative part of the
-    curve, where it falls from 1 towards the noise).  The cost
+    Annuli b = 1, 2, ... inside the cutoff (b < r, where the model is
+    defined) are used until the first with den_b <= 0 or an observed ratio
+    num_b/den_b below SEEING_STOP (the informative part of the curve, where
+    it falls from 1 towards the noise).  The cost
     J(x) = sum_b (num_b/den_b - ratio_model(b/r, x))^2 is evaluated on the
     SEEING_GRID candidates; the first minimum is refined by a parabola through
     it and its neighbours in log x (not at the ends of the grid).  With no
@@ -388,11 +389,11 @@ def fit_d_over_r0(num: np.ndarray, den: np.ndarray, N: int, fc: float, ck: float
     r = cutoff_radius(N, fc)
     bins = []
     for b in range(1, len(num)):
-        if not den[b] > 0.0 or num[b] / den[b] < SEEING_STOP:
+        if not b < r or not den[b] > 0.0 or num[b] / den[b] < SEEING_STOP:
             break
         bins.append(b)
     lo, hi, n = SEEING_GRID
-    lx = np.log(lo) + (np.log(hi) - np.log(lo)) * np.arange(n) / (n - 1)
+    lx = np.log(lo) + (np.log(hi) - np.log(lo)) * (np.arange(n) / (n - 1))
     if not bins:
         return float(hi)
     bins = np.array(bins)
