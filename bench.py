@@ -117,14 +117,21 @@ from oracle import speckle_oracle as O
 spec = CONFIGS[{cfg!r}]
 b = make_burst(spec, F={max(frames_small)}, burst=99)
 subs = O.subfield_grid(spec.W, spec.H, {N}, {N} // 2)
+cubes = O.seeing_cubes(spec.W, spec.H, {N}, {N} // 2)
 s = len(subs) // 2
+c = cubes[len(cubes) // 2]
 stf = O.stf_model({N}, 0.2885, b['d_over_r0'])
 t = []
 for F in {tuple(frames_small)!r}:
     t0 = time.perf_counter()
     O.reconstruct_subfield(b['frames'][:F], subs[s], {N}, 0.2885, {R}, {N} // 8, stf)
-    t.append(time.perf_counter() - t0)
-print(json.dumps({{"t": t, "n_sub": len(subs), "F": spec.F}}))
+    t1 = time.perf_counter()
+    In, _, _ = O.frame_spectra(b['frames'][:F], subs[c], {N}, {N} // 8)
+    P, M = O.power_mean(In)
+    num, den = O.spectral_ratio(P, M, O.noise_floor(P, {N}, 0.2885), F, {N}, 0.2885)
+    O.fit_d_over_r0(num, den, {N}, 0.2885)
+    t.append((t1 - t0, time.perf_counter() - t1))
+print(json.dumps({{"t": t, "n_sub": len(subs), "n_cubes": len(cubes), "F": spec.F}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -132,15 +139,20 @@ print(json.dumps({{"t": t, "n_sub": len(subs), "F": spec.F}}))
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    (f1, f2), (t1, t2) = frames_small, d["t"]
-    per_frame = max((t2 - t1) / (f2 - f1), 0.0)
-    fixed = max(t1 - f1 * per_frame, 0.0)
-    per_burst = d["n_sub"] * (fixed + d["F"] * per_frame)
+    (f1, f2) = frames_small
+
+    def extrapolate(t1, t2):           # linear in F, to the workload's F
+        per_frame = max((t2 - t1) / (f2 - f1), 0.0)
+        return max(t1 - f1 * per_frame, 0.0) + d["F"] * per_frame
+
+    (a1, s1), (a2, s2) = d["t"]
+    per_burst = d["n_sub"] * extrapolate(a1, a2) + d["n_cubes"] * extrapolate(s1, s2)
     return {"value": 1.0 / per_burst, "unit": "bursts/s", "cores": 1, "kind": "oracle",
             "sample": (f"FP64 numpy oracle, 1 thread: one {N}x{N} subfield at F={f1} and F={f2} "
-                       f"({t1:.2f} s, {t2:.2f} s), extrapolated linearly in F to {d['F']} frames "
-                       f"x {d['n_sub']} subfields = {per_burst:.0f} s per burst"),
-            "seconds": t1 + t2}
+                       f"({a1:.2f} s, {a2:.2f} s) and one seeing cube ({s1:.2f} s, {s2:.2f} s), "
+                       f"extrapolated linearly in F to {d['F']} frames x {d['n_sub']} subfields + "
+                       f"{d['n_cubes']} cubes = {per_burst:.0f} s per burst"),
+            "seconds": a1 + a2 + s1 + s2}
 
 
 def run_reference(args):
@@ -198,13 +210,12 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps):
     frames = [torch.from_numpy(tio_burst["frames"]).pin_memory(), None,
               torch.from_numpy(hb["frames"]).pin_memory()]
     frames[1] = frames[0]
-    r0 = [tio_burst["d_over_r0"], tio_burst["d_over_r0"], hb["d_over_r0"]]
     eng = Engine(chans, hbm_budget_bytes=int(120e9), max_inflight=3, device=local)
     outs = {c: [torch.empty((chans[c].H, chans[c].W), dtype=torch.float32).pin_memory() for _ in range(3)]
             for c in range(3)}
     # warm up every channel once
     for c in range(3):
-        t = eng.submit(c, frames[c].numpy(), outs[c][0].numpy(), d_over_r0=r0[c])
+        t = eng.submit(c, frames[c].numpy(), outs[c][0].numpy())        # seeing estimated per burst
         eng.poll(t, -1)
     n = max(30, 6 * steps)
     rate = 0.6 * capacity                      # offered load: 60 % of the measured capacity
@@ -221,7 +232,7 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps):
         while queue:
             i = queue[0]
             c = int(chan[i])
-            tk = eng.try_submit(c, frames[c].numpy(), outs[c][i % 3].numpy(), d_over_r0=r0[c])
+            tk = eng.try_submit(c, frames[c].numpy(), outs[c][i % 3].numpy())
             if tk is None:
                 break
             pending.append((tk, i))
@@ -295,11 +306,10 @@ def main():
     plan = Plan(ch, device=local)
     info = plan.info
     n_sub = info["n_sub"]
-    stf_np = plan.model_stf(b["d_over_r0"])
     dev = torch.device("cuda", local)
     frames = torch.from_numpy(b["frames"]).to(dev)
-    stf = torch.from_numpy(stf_np).to(dev)
     ws, lay = plan.workspace(F, n_sub)
+    stf = plan.views(ws, lay, F, n_sub)["stf"]       # written by the seeing stage
     out = torch.empty((spec.H, spec.W), dtype=torch.float32, device=dev)
     valid = torch.empty((spec.H, spec.W), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -307,6 +317,8 @@ def main():
     def step(ev=None):
         plan.stage_spectra(frames, F, 0, n_sub, ws, lay, stream)
         plan.stage_stats(F, n_sub, ws, lay, stream)
+        plan.stage_seeing(F, 0, n_sub, ws, lay, stream)      # Sect. 3.1: r0 from the burst itself
+        plan.stage_seeing_stf(ws, lay, stream)
         plan.stage_amplitude(n_sub, stf, ws, lay, stream)
         if ev is not None:
             ev[0].record(stream)
@@ -317,7 +329,7 @@ def main():
         plan.stage_inverse(F, 0, n_sub, ws, lay, stream)
         plan.stage_mosaic(ws, lay, out, valid, stream)
 
-    launches_per_step = 7
+    launches_per_step = 9
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -373,7 +385,6 @@ def main():
         host_valid = [torch.empty((spec.H, spec.W), dtype=torch.uint8).pin_memory() for _ in range(2)]
         eng = Engine([ch], hbm_budget_bytes=int(100e9), max_inflight=2, device=local)
         fr_np = host_frames.numpy()
-        d_r0 = b["d_over_r0"]
 
         def serve(n):
             pending, lat = [], []
@@ -382,8 +393,7 @@ def main():
             while done < n:
                 while submitted < n and len(pending) < 2:
                     k = submitted % 2
-                    tk = eng.try_submit(0, fr_np, host_out[k].numpy(), host_valid[k].numpy(),
-                                        d_over_r0=d_r0)
+                    tk = eng.try_submit(0, fr_np, host_out[k].numpy(), host_valid[k].numpy())
                     if tk is None:
                         break
                     pending.append((tk, time.perf_counter()))
@@ -401,7 +411,7 @@ def main():
         el_max = max_over_ranks(el, dev)
         eng.close()
         e2e = {"value": whole_job_rate(args.steps, world, el_max), "unit": "bursts/s",
-               "h2d_bytes_per_step": int(b["frames"].nbytes + N * N * 8),
+               "h2d_bytes_per_step": int(b["frames"].nbytes),
                "d2h_bytes_per_step": int(spec.W * spec.H * 5),
                "latency_ms_p50": 1000 * float(np.percentile(lat, 50)),
                "latency_ms_p99": 1000 * float(np.percentile(lat, 99)),
@@ -427,6 +437,8 @@ def main():
                 "config": {"workload": f"{args.workload} burst: {spec.W}x{spec.H}x{F} uint16, "
                                        f"{n_sub} subfields of {N}^2 at 50% overlap, |v|<={R}",
                            "path": "plain per-burst stages, FP32 spectra and arithmetic",
+                           "seeing": "estimated from each burst (spectral ratio over the non-overlapping "
+                                     f"{N}^2 cubes, {info['n_cubes']} cubes)",
                            "l2": "inputs larger than L2 (no flush)",
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": launches_per_step * args.steps,

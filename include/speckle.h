@@ -95,6 +95,7 @@ typedef struct {
     int    n_points;       /* recursion points in H with |w|^2 >= 2            */
     int    n_U;            /* |U|                                              */
     int    n_V;            /* |V|                                              */
+    int    n_cubes;        /* seeing cubes: full-size subfields on the N grid  */
 } sm_plan_info;
 
 /* Build a plan on `device`.  Validates every field of *ch (SM_EINVAL). */
@@ -103,6 +104,13 @@ int sm_plan_destroy(sm_plan* plan);
 int sm_plan_get_info(const sm_plan* plan, sm_plan_info* info);
 /* Subfield rectangles (x0, y0, w, h) in host memory, [n_sub][4] ints. */
 int sm_plan_subfields(const sm_plan* plan, int* xywh);
+
+/* Seeing cubes (Sect. 3.1): the burst cut into non-overlapping N x N cubes
+ * from the image origin (80 for a 2560 x 2160 burst of N = 256).  They are
+ * the full-size subfields whose corner lies on the N grid, so there are
+ * some only when the stride divides N.  sub_idx: host int[n_cubes] gets
+ * their subfield indices, in cube order.                                    */
+int sm_plan_cubes(const sm_plan* plan, int* sub_idx);
 
 /* Position of the bispectrum value B(w - v, v) of pair (w, v) in the per-
  * subfield B buffer (units of complex values), for n host pairs given as
@@ -127,6 +135,9 @@ typedef struct {
     size_t B;      /* [nsub][n_tiles][tile_pairs] float2: mean bispectrum     */
     size_t z;      /* [nsub][hb_rows][box_pitch] double2: unit phasors        */
     size_t rec;    /* [n_sub total][N][N] float: sub-images of all subfields  */
+    size_t seeing; /* [n_cubes + 1] double: D/r0 of every seeing cube, then the
+                    * burst's D / mean r0                                    */
+    size_t stf;    /* [N][N] double, centred: model STF at the burst's seeing */
     size_t bytes;  /* total workspace size                                    */
 } sm_workspace_layout;
 
@@ -155,6 +166,25 @@ int sm_stage_stats(const sm_plan* plan, int F, int nsub, void* ws,
 int sm_stage_amplitude(const sm_plan* plan, int nsub, const double* stf, void* ws,
                        const sm_workspace_layout* lay, void* stream);
 
+/* Sect. 3.1 (spectral ratio technique, von der Luehe 1984): D/r0 of every
+ * seeing cube among subfields sub0..sub0+nsub-1 (after sm_stage_stats of
+ * that chunk), into seeing[cube].  Per cube, over annuli b of unit width
+ * in the half-plane domain: num_b = sum (F |M|^2 - P) / (F - 1) and
+ * den_b = sum (P - noise); annuli b = 1, 2, ... are used until the first
+ * with den_b <= 0 or num_b / den_b < 0.05; D/r0 = x minimises
+ * sum_b (num_b/den_b - |T_LE(b/r; x)|^2 / STF(b/r; x))^2 over 256
+ * log-spaced candidates in [1, 64] (Fried long-exposure OTF, the model STF
+ * of sm_model_stf, both 1 at k = 0), refined by a parabola in log x; 64
+ * when no annulus qualifies.  FP64.  Needs F >= 2 and a plan with cubes.   */
+int sm_stage_seeing(const sm_plan* plan, int F, int sub0, int nsub, void* ws,
+                    const sm_workspace_layout* lay, void* stream);
+
+/* Sect. 3.1: the burst's seeing is the mean r0 of the cubes,
+ * seeing[n_cubes] = 1 / mean_c (1 / seeing[c]), and stf gets the model STF
+ * of sm_model_stf at that D/r0 (device double [N][N], centred) for
+ * sm_stage_amplitude.  Every cube's seeing must be written first.          */
+int sm_stage_seeing_stf(const sm_plan* plan, void* ws, const sm_workspace_layout* lay, void* stream);
+
 /* Sect. 2, 3.2 (speckle masking): mean bispectrum
  * B(w-v, v) = (1/F) sum_i I_i(w-v) I_i(v) conj I_i(w) on every pair the
  * phase recursion reads.                                                    */
@@ -178,7 +208,12 @@ int sm_stage_mosaic(const sm_plan* plan, void* ws, const sm_workspace_layout* la
                     float* out, uint8_t* valid, void* stream);
 
 /* Whole path on device data: chunks of lay->... subfields through every
- * stage, then the mosaic.  Asynchronous on `stream`.                       */
+ * stage, then the mosaic.  Asynchronous on `stream`.  stf: device
+ * [N][N] centred table, or NULL to estimate the seeing from the burst
+ * (Sect. 3.1: sm_stage_seeing on every chunk holding cubes, then
+ * sm_stage_seeing_stf; when the chunks do not cover every subfield at once
+ * the spectra of the cube chunks are computed twice).  SM_EINVAL when
+ * stf is NULL and the plan has no cube or F < 2.                           */
 int sm_reconstruct(const sm_plan* plan, const void* frames, int frame_type, int F,
                    const double* stf, int nsub_chunk, void* ws,
                    const sm_workspace_layout* lay, float* out, uint8_t* valid, void* stream);
@@ -233,7 +268,9 @@ typedef struct {
     int            frame_type;          /* SM_U16 / SM_F32                        */
     int            frames_on_device;    /* 1: frames is a device pointer          */
     const double*  stf;                 /* host [N][N] centred, or NULL           */
-    const double*  d_over_r0;           /* host [F]; used when stf == NULL        */
+    const double*  d_over_r0;           /* host [F]; used when stf == NULL; with
+                                         * both NULL the seeing is estimated on
+                                         * the device (sm_stage_seeing)           */
     float*         out;                 /* host [H][W], caller-owned              */
     uint8_t*       valid;               /* host [H][W] or NULL                    */
 } sm_burst;
@@ -244,6 +281,8 @@ typedef struct {
     double t_done_ms;                   /* engine clock when the result was ready */
     double gpu_ms;                      /* device time of the burst's work        */
     size_t bytes_admitted;              /* device bytes held by the burst         */
+    double d_over_r0;                   /* the burst's estimated D / mean r0, or 0
+                                         * when the STF or D/r0 was given         */
 } sm_result;
 
 int sm_open(const sm_config* cfg, sm_handle** out);

@@ -88,6 +88,12 @@ class Plan:
         check(self.lib.sm_plan_subfields(self.h, out.ctypes.data), "sm_plan_subfields")
         return out
 
+    def cubes(self) -> np.ndarray:
+        """Subfield indices of the seeing cubes (sm_plan_cubes)."""
+        out = np.zeros(self.info["n_cubes"], dtype=np.int32)
+        check(self.lib.sm_plan_cubes(self.h, out.ctypes.data if len(out) else None), "sm_plan_cubes")
+        return out
+
     def pair_index(self, wv: np.ndarray) -> np.ndarray:
         wv = np.ascontiguousarray(wv, dtype=np.int32).reshape(-1, 4)
         idx = np.zeros(len(wv), dtype=np.int64)
@@ -145,6 +151,8 @@ class Plan:
                    (nsub, i["n_tiles"] * i["tile_pairs"])),
             "z": v(lay.z, nsub * hb, torch.complex128, (nsub, i["hb_rows"], i["box_pitch"])),
             "rec": v(lay.rec, i["n_sub"] * N * N, torch.float32, (i["n_sub"], N, N)),
+            "seeing": v(lay.seeing, i["n_cubes"] + 1, torch.float64, (i["n_cubes"] + 1,)),
+            "stf": v(lay.stf, N * N, torch.float64, (N, N)),
         }
 
     # ---- stage entry points (device tensors) -------------------------------
@@ -160,6 +168,14 @@ class Plan:
     def stage_amplitude(self, nsub, stf, ws, lay, stream=None):
         check(self.lib.sm_stage_amplitude(self.h, nsub, _ptr(stf), _ptr(ws), C.byref(lay), _stream(stream)),
               "sm_stage_amplitude")
+
+    def stage_seeing(self, F, sub0, nsub, ws, lay, stream=None):
+        check(self.lib.sm_stage_seeing(self.h, F, sub0, nsub, _ptr(ws), C.byref(lay), _stream(stream)),
+              "sm_stage_seeing")
+
+    def stage_seeing_stf(self, ws, lay, stream=None):
+        check(self.lib.sm_stage_seeing_stf(self.h, _ptr(ws), C.byref(lay), _stream(stream)),
+              "sm_stage_seeing_stf")
 
     def stage_bispectrum(self, F, nsub, ws, lay, stream=None):
         check(self.lib.sm_stage_bispectrum(self.h, F, nsub, _ptr(ws), C.byref(lay), _stream(stream)),
@@ -177,6 +193,7 @@ class Plan:
                                        _stream(stream)), "sm_stage_mosaic")
 
     def reconstruct(self, frames, F, stf, chunk, ws, lay, out, valid=None, stream=None):
+        """sm_reconstruct; stf None estimates the seeing from the burst (Sect. 3.1)."""
         ft = SM_U16 if str(frames.dtype).endswith("uint16") else SM_F32
         check(self.lib.sm_reconstruct(self.h, _ptr(frames), ft, F, _ptr(stf), chunk, _ptr(ws), C.byref(lay),
                                       _ptr(out), _ptr(valid), _stream(stream)), "sm_reconstruct")
@@ -209,7 +226,10 @@ class Engine:
 
     def submit(self, channel: int, frames, out: np.ndarray, valid: Optional[np.ndarray] = None,
                stf: Optional[np.ndarray] = None, d_over_r0: Optional[np.ndarray] = None) -> int:
-        """Returns a ticket, or raises SpeckleError (status SM_EBUSY when no slot is free)."""
+        """Returns a ticket, or raises SpeckleError (status SM_EBUSY when no slot is free).
+
+        With neither ``stf`` nor ``d_over_r0`` the seeing is estimated on the
+        device from the burst itself (Sect. 3.1)."""
         on_dev = not isinstance(frames, np.ndarray)
         ft = SM_U16 if str(frames.dtype).endswith("uint16") else SM_F32
         stf = None if stf is None else np.ascontiguousarray(stf, dtype=np.float64)
@@ -237,7 +257,7 @@ class Engine:
         check(st, "sm_poll")
         self._keep.pop(ticket, None)
         return st, {"t_submit_ms": res.t_submit_ms, "t_done_ms": res.t_done_ms, "gpu_ms": res.gpu_ms,
-                    "bytes_admitted": res.bytes_admitted}
+                    "bytes_admitted": res.bytes_admitted, "d_over_r0": res.d_over_r0}
 
     def close(self):
         if self.h:

@@ -31,12 +31,12 @@ class sm_plan_info(C.Structure):
                 ("R", C.c_int), ("box_rows", C.c_int), ("box_cols", C.c_int), ("box_pitch", C.c_int),
                 ("hb_rows", C.c_int), ("n_tiles", C.c_int), ("tile_pairs", C.c_int),
                 ("n_pairs", C.c_longlong), ("n_rings", C.c_int), ("n_points", C.c_int),
-                ("n_U", C.c_int), ("n_V", C.c_int)]
+                ("n_U", C.c_int), ("n_V", C.c_int), ("n_cubes", C.c_int)]
 
 
 class sm_workspace_layout(C.Structure):
     _fields_ = [(n, C.c_size_t) for n in
-                ("spec", "flux", "mu", "P", "M", "noise", "A", "B", "z", "rec", "bytes")]
+                ("spec", "flux", "mu", "P", "M", "noise", "A", "B", "z", "rec", "seeing", "stf", "bytes")]
 
 
 class sm_config(C.Structure):
@@ -52,7 +52,7 @@ class sm_burst(C.Structure):
 
 class sm_result(C.Structure):
     _fields_ = [("status", C.c_int), ("t_submit_ms", C.c_double), ("t_done_ms", C.c_double),
-                ("gpu_ms", C.c_double), ("bytes_admitted", C.c_size_t)]
+                ("gpu_ms", C.c_double), ("bytes_admitted", C.c_size_t), ("d_over_r0", C.c_double)]
 
 
 _P = C.c_void_p
@@ -65,11 +65,14 @@ SIGNATURES = {
     "sm_plan_destroy": (_I, [_P]),
     "sm_plan_get_info": (_I, [_P, C.POINTER(sm_plan_info)]),
     "sm_plan_subfields": (_I, [_P, _P]),
+    "sm_plan_cubes": (_I, [_P, _P]),
     "sm_plan_pair_index": (_I, [_P, C.c_longlong, _P, _P]),
     "sm_workspace_query": (_I, [_P, _I, _I, _LAY]),
     "sm_stage_spectra": (_I, [_P, _P, _I, _I, _I, _I, _P, _LAY, _P]),
     "sm_stage_stats": (_I, [_P, _I, _I, _P, _LAY, _P]),
     "sm_stage_amplitude": (_I, [_P, _I, _P, _P, _LAY, _P]),
+    "sm_stage_seeing": (_I, [_P, _I, _I, _I, _P, _LAY, _P]),
+    "sm_stage_seeing_stf": (_I, [_P, _P, _LAY, _P]),
     "sm_stage_bispectrum": (_I, [_P, _I, _I, _P, _LAY, _P]),
     "sm_stage_phase": (_I, [_P, _I, _P, _LAY, _P]),
     "sm_stage_inverse": (_I, [_P, _I, _I, _I, _P, _LAY, _P]),

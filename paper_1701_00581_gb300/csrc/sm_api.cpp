@@ -92,6 +92,8 @@ extern "C" int sm_workspace_query(const sm_plan* plan, int F, int nsub_chunk, sm
     lay->B = o; o += al(n * d.n_tiles * (size_t)TILE_PAIRS * sizeof(float2));
     lay->z = o; o += al(n * hb * sizeof(double2));
     lay->rec = o; o += al((size_t)d.n_sub * d.N * d.N * sizeof(float));
+    lay->seeing = o; o += al((size_t)(d.n_cubes + 1) * sizeof(double));
+    lay->stf = o; o += al((size_t)d.N * d.N * sizeof(double));
     lay->bytes = o;
     return SM_OK;
 }
@@ -130,6 +132,33 @@ extern "C" int sm_stage_amplitude(const sm_plan* plan, int nsub, const double* s
     return ret(smk::launch_amplitude(plan->dev, nsub, stf, at<float>(ws, lay->P), at<float>(ws, lay->noise),
                                      at<float>(ws, lay->A), (cudaStream_t)stream),
                "amplitude kernel");
+}
+
+extern "C" int sm_stage_seeing(const sm_plan* plan, int F, int sub0, int nsub, void* ws,
+                               const sm_workspace_layout* lay, void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (F < 2) { set_error("the spectral ratio needs F >= 2"); return SM_EINVAL; }
+    if (plan->dev.n_cubes < 1) {
+        set_error("no seeing cube: the stride must divide N and the image hold an N x N cube"); return SM_EINVAL;
+    }
+    if (sub0 < 0 || nsub < 1 || sub0 + nsub > plan->dev.n_sub) { set_error("subfield range"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_seeing(plan->dev, F, sub0, nsub, at<float>(ws, lay->P), at<float2>(ws, lay->M),
+                                  at<float>(ws, lay->noise), at<double>(ws, lay->seeing), (cudaStream_t)stream),
+               "seeing kernel");
+}
+
+extern "C" int sm_stage_seeing_stf(const sm_plan* plan, void* ws, const sm_workspace_layout* lay, void* stream) {
+    int rc = check_lay(plan, ws, lay);
+    if (rc) return rc;
+    if (plan->dev.n_cubes < 1) {
+        set_error("no seeing cube: the stride must divide N and the image hold an N x N cube"); return SM_EINVAL;
+    }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_seeing_stf(plan->dev, at<double>(ws, lay->seeing), at<double>(ws, lay->stf),
+                                      (cudaStream_t)stream),
+               "seeing STF kernel");
 }
 
 extern "C" int sm_stage_bispectrum(const sm_plan* plan, int F, int nsub, void* ws,
@@ -183,10 +212,38 @@ extern "C" int sm_reconstruct(const sm_plan* plan, const void* frames, int frame
     if (rc) return rc;
     const int n = plan->dev.n_sub;
     if (nsub_chunk < 1 || nsub_chunk > n) { set_error("nsub_chunk out of range"); return SM_EINVAL; }
+    // Seeing from the burst itself (Sect. 3.1) when no STF is given: with one
+    // chunk the cubes are estimated inside it; otherwise a first pass over
+    // the chunks holding cubes estimates them before any modulus is formed.
+    const bool est = stf == nullptr;
+    if (est) {
+        if (plan->dev.n_cubes < 1) {
+            set_error("no STF given and no seeing cube to estimate it (the stride must divide N)");
+            return SM_EINVAL;
+        }
+        if (F < 2) { set_error("no STF given and F < 2: the seeing estimate needs two frames"); return SM_EINVAL; }
+        stf = at<double>(ws, lay->stf);
+        if (nsub_chunk < n) {
+            for (int s0 = 0; s0 < n; s0 += nsub_chunk) {
+                const int ns = std::min(nsub_chunk, n - s0);
+                bool cubes = false;
+                for (int s = s0; s < s0 + ns; ++s) cubes |= plan->cube_of_sub[s] >= 0;
+                if (!cubes) continue;
+                if ((rc = sm_stage_spectra(plan, frames, frame_type, F, s0, ns, ws, lay, stream))) return rc;
+                if ((rc = sm_stage_stats(plan, F, ns, ws, lay, stream))) return rc;
+                if ((rc = sm_stage_seeing(plan, F, s0, ns, ws, lay, stream))) return rc;
+            }
+            if ((rc = sm_stage_seeing_stf(plan, ws, lay, stream))) return rc;
+        }
+    }
     for (int s0 = 0; s0 < n; s0 += nsub_chunk) {
         const int ns = std::min(nsub_chunk, n - s0);
         if ((rc = sm_stage_spectra(plan, frames, frame_type, F, s0, ns, ws, lay, stream))) return rc;
         if ((rc = sm_stage_stats(plan, F, ns, ws, lay, stream))) return rc;
+        if (est && nsub_chunk >= n) {
+            if ((rc = sm_stage_seeing(plan, F, s0, ns, ws, lay, stream))) return rc;
+            if ((rc = sm_stage_seeing_stf(plan, ws, lay, stream))) return rc;
+        }
         if ((rc = sm_stage_amplitude(plan, ns, stf, ws, lay, stream))) return rc;
         if ((rc = sm_stage_bispectrum(plan, F, ns, ws, lay, stream))) return rc;
         if ((rc = sm_stage_phase(plan, ns, ws, lay, stream))) return rc;
@@ -254,6 +311,7 @@ struct Job {
     uint8_t* host_valid = nullptr;
     float* d_out = nullptr;
     uint8_t* d_valid = nullptr;
+    const double* d_seeing = nullptr;     // the burst's D / mean r0 when estimated
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
     double t_submit = 0.0;
     int status = SM_PENDING;
@@ -321,11 +379,13 @@ void finish_job(sm_handle* h, Job& j) {
 namespace {
 
 // Launch one burst's stage sequence on its slot stream through a cached
-// CUDA graph (captured on first use of the key).  The frame type is part of
-// the captured kernels, so it joins the key through the channel's F slot.
+// CUDA graph (captured on first use of the key).  The frame type and the
+// STF mode (given, or estimated on the device when d_stf is NULL) are part
+// of the captured kernels, so they join the key through the F slot.
 int launch_burst(sm_handle* h, const sm_burst* b, const Job& j, const void* d_frames, const double* d_stf,
                  void* ws, sm_workspace_layout& lay, cudaStream_t st) {
-    const auto key = std::make_tuple(b->channel, b->F * 2 + (b->frame_type == SM_F32 ? 1 : 0), j.off, j.slot);
+    const auto key = std::make_tuple(b->channel, b->F * 4 + (d_stf ? 0 : 2) + (b->frame_type == SM_F32 ? 1 : 0),
+                                     j.off, j.slot);
     cudaGraphExec_t exec = nullptr;
     {
         std::lock_guard<std::mutex> lk(h->mu);
@@ -415,16 +475,20 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     const sm_channel& ch = h->ch[b->channel];
     if (b->F < 1 || b->F > ch.max_frames || !b->frames || !b->out) { set_error("bad burst"); return SM_EINVAL; }
     if (b->frame_type != SM_U16 && b->frame_type != SM_F32) { set_error("bad frame_type"); return SM_EINVAL; }
-    if (!b->stf && !b->d_over_r0) { set_error("need stf or d_over_r0"); return SM_EINVAL; }
+    const bool est = !b->stf && !b->d_over_r0;     // seeing estimated on the device (Sect. 3.1)
+    if (est && (h->plans[b->channel]->dev.n_cubes < 1 || b->F < 2)) {
+        set_error("no stf or d_over_r0, and the seeing cannot be estimated (needs a cube and F >= 2)");
+        return SM_EINVAL;
+    }
     const auto t_in = Clock::now();
     std::vector<double> stf;
-    if (!b->stf) {
+    if (!b->stf && !est) {
         stf.resize((size_t)ch.N * ch.N);
         int rc = sm_model_stf(&ch, b->F, b->d_over_r0, stf.data());
         if (rc) return rc;
     }
     const double t_stf = ms_since(t_in);
-    const double* stf_src = b->stf ? b->stf : stf.data();
+    const double* stf_src = b->stf ? b->stf : (est ? nullptr : stf.data());
     DeviceGuard g(h->cfg.device);
     sm_workspace_layout lay;
     const size_t need = burst_bytes(h, b->channel, b->F, &lay);
@@ -455,6 +519,7 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     double* d_stf = reinterpret_cast<double*>(reinterpret_cast<char*>(j.d_valid) + al((size_t)ch.W * ch.H));
     j.channel = b->channel;
     j.F = b->F;
+    if (est) j.d_seeing = at<double>(ws, lay.seeing) + h->plans[b->channel]->dev.n_cubes;
     j.host_out = b->out;
     j.host_valid = b->valid;
     cudaError_t e = cudaEventCreate(&j.ev_start);
@@ -465,7 +530,7 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
         else
             e = cudaMemcpyAsync(d_frames, b->frames, fbytes, cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !est) {
         // from pinned staging: a pageable source would make the copy wait
         // behind the frame transfer and other pageable traffic
         double* pin = h->stf_pinned[j.slot];
@@ -480,7 +545,7 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "staging burst");
     } else {
-        rc = launch_burst(h, b, j, d_frames, d_stf, ws, lay, st);
+        rc = launch_burst(h, b, j, d_frames, est ? nullptr : d_stf, ws, lay, st);
         if (rc == SM_OK) {
             e = cudaEventRecord(j.ev_done, st);
             if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
@@ -542,6 +607,8 @@ extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result*
     const size_t npx = (size_t)ch.W * ch.H;
     cudaError_t e = cudaMemcpy(j.host_out, j.d_out, npx * sizeof(float), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && j.host_valid) e = cudaMemcpy(j.host_valid, j.d_valid, npx, cudaMemcpyDeviceToHost);
+    double dr0 = 0.0;
+    if (e == cudaSuccess && j.d_seeing) e = cudaMemcpy(&dr0, j.d_seeing, sizeof(double), cudaMemcpyDeviceToHost);
     float gms = 0.f;
     cudaEventElapsedTime(&gms, j.ev_start, j.ev_done);
     int rc = e == cudaSuccess ? SM_OK : cuda_fail(e, "copying the mosaic");
@@ -551,6 +618,7 @@ extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result*
         res->t_done_ms = t_done;
         res->gpu_ms = gms;
         res->bytes_admitted = j.bytes;
+        res->d_over_r0 = dr0;
     }
     finish_job(h, j);
     h->jobs.erase(it);

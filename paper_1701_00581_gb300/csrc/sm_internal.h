@@ -58,6 +58,14 @@ struct PlanDev {
     const int4* point_rec;      // [n_points] (wx, wy, first item, end item), items counted
                                 //   from the first item of the point's ring
     int n_items, max_ring_items, max_ring_points;
+    // seeing (Sect. 3.1): the non-overlapping N x N cubes among the
+    // subfields and the annuli of unit width over the half-plane domain
+    int n_cubes;
+    double rcut, ck;         // cutoff radius fc N in DFT bins; Korff constant of the model STF
+    const int* cube_of_sub;  // [n_sub] cube index or -1
+    int n_bins;              // K + 2 annuli b = 0..K+1 (nearest integer |k|)
+    const int* ann_start;    // [n_bins + 1] CSR over ann_idx
+    const int* ann_idx;      // half-box element index (ky * box_pitch + kx + K), row-major per annulus
     const double* t0;        // [hb_rows][box_pitch] diffraction OTF on the half box
 };
 
@@ -72,6 +80,10 @@ cudaError_t launch_stats(const smi::PlanDev& p, const void* spec, int F, int nsu
                          float2* M, float* noise, cudaStream_t st);
 cudaError_t launch_amplitude(const smi::PlanDev& p, int nsub, const double* stf, const float* P,
                              const float* noise, float* A, cudaStream_t st);
+cudaError_t launch_seeing(const smi::PlanDev& p, int F, int sub0, int nsub, const float* P, const float2* M,
+                          const float* noise, double* seeing, cudaStream_t st);
+cudaError_t launch_seeing_stf(const smi::PlanDev& p, double* seeing, double* stf, cudaStream_t st);
+int seeing_max_bins();   // annuli the seeing kernel holds in shared memory
 cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, int nsub,
                               float2* B, cudaStream_t st);
 cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M,

@@ -200,6 +200,40 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
                 }
         }
     d.n_tiles = (int)pl->tiles.size();
+
+    // seeing cubes (Sect. 3.1): non-overlapping N x N tiles from the image
+    // origin, i.e. the full-size subfields whose corner lies on the N grid
+    pl->cube_of_sub.assign(d.n_sub, -1);
+    for (int s = 0; s < d.n_sub; ++s) {
+        const int4 q = pl->subs[s];
+        if (q.x % N == 0 && q.y % N == 0 && q.z == N && q.w == N) {
+            pl->cube_of_sub[s] = (int)pl->cubes.size();
+            pl->cubes.push_back(s);
+        }
+    }
+    d.n_cubes = (int)pl->cubes.size();
+    d.rcut = r;
+    d.ck = ch->ck;
+    // annuli b = nearest integer |k| over U n H: (2b - 1)^2 <= 4|k|^2 < (2b + 1)^2
+    d.n_bins = K + 2;
+    if (d.n_bins > smk::seeing_max_bins()) { delete pl; set_error("fc*N too large for the seeing annuli"); return SM_EINVAL; }
+    {
+        std::vector<std::vector<int>> ann(d.n_bins);
+        for (int ky = 0; ky <= K; ++ky)
+            for (int kx = -K; kx <= K; ++kx) {
+                const int q = kx * kx + ky * ky;
+                if (q > r2i || !(ky > 0 || (ky == 0 && kx > 0))) continue;
+                int sq = (int)std::sqrt((double)(4 * q));
+                while (sq * sq > 4 * q) --sq;
+                while ((sq + 1) * (sq + 1) <= 4 * q) ++sq;
+                ann[(sq + 1) / 2].push_back(ky * d.box_pitch + kx + K);
+            }
+        pl->ann_start.assign(d.n_bins + 1, 0);
+        for (int b = 0; b < d.n_bins; ++b) {
+            pl->ann_start[b + 1] = pl->ann_start[b] + (int)ann[b].size();
+            pl->ann_idx.insert(pl->ann_idx.end(), ann[b].begin(), ann[b].end());
+        }
+    }
     // The bispectrum kernel stages W and U = W - V in 16-byte copies from even
     // box columns of an even-pitched box.
     for (const int4& T : pl->tiles)
@@ -305,6 +339,9 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         {pl->point_items.data(), pl->point_items.size() * sizeof(int), 0},
         {winft.data(), winft.size() * sizeof(float2), 0},
         {pl->point_rec.data(), pl->point_rec.size() * sizeof(int4), 0},
+        {pl->cube_of_sub.data(), pl->cube_of_sub.size() * sizeof(int), 0},
+        {pl->ann_start.data(), pl->ann_start.size() * sizeof(int), 0},
+        {pl->ann_idx.data(), pl->ann_idx.size() * sizeof(int), 0},
     };
     size_t total = 0;
     for (auto& p : pcs) { p.off = total; total += align256(std::max<size_t>(p.bytes, 1)); }
@@ -334,6 +371,9 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.point_items = (const int*)at(13);
     d.winft = (const float2*)at(14);
     d.point_rec = (const int4*)at(15);
+    d.cube_of_sub = (const int*)at(16);
+    d.ann_start = (const int*)at(17);
+    d.ann_idx = (const int*)at(18);
     *out = pl;
     return SM_OK;
 }
@@ -360,6 +400,13 @@ extern "C" int sm_plan_get_info(const sm_plan* plan, sm_plan_info* info) {
     info->n_pairs = plan->n_pairs;
     info->n_rings = d.n_rings; info->n_points = d.n_points;
     info->n_U = plan->n_U; info->n_V = plan->n_V;
+    info->n_cubes = d.n_cubes;
+    return SM_OK;
+}
+
+extern "C" int sm_plan_cubes(const sm_plan* plan, int* sub_idx) {
+    if (!plan || (!sub_idx && plan->dev.n_cubes > 0)) { set_error("NULL argument"); return SM_EINVAL; }
+    for (int c = 0; c < plan->dev.n_cubes; ++c) sub_idx[c] = plan->cubes[c];
     return SM_OK;
 }
 

@@ -161,3 +161,24 @@ def test_halpha_whole_subfields(torch):
         Bg = v["B"][s].cpu().numpy()[idx]
         assert CS.rel_l2(Bg, CS.oracle_B_used(o["In"], wv)) < SPEC_TOL
         assert CS.rel_l2(v["rec"][s].cpu().numpy(), o["rec"]) < IMG_TOL
+
+
+def test_tio_seeing_on_the_80_cubes(tio, torch):
+    """Sect. 3.1: the 2560 x 2160 burst's 80 non-overlapping 256^2 cubes,
+    each cube's fitted D/r0 against the oracle fit on the same statistics."""
+    from oracle import speckle_oracle as O
+    from .test_gpu_seeing import FIT_TOL, oracle_fit_on_gpu_stats
+    plan, v, spec = tio["plan"], tio["views"], tio["spec"]
+    n = plan.info["n_sub"]
+    lay = plan.layout(spec.F, n)
+    assert plan.info["n_cubes"] == 80
+    assert plan.cubes().tolist() == O.seeing_cubes(spec.W, spec.H, 256, 128)
+    plan.stage_seeing(spec.F, 0, n, tio["ws"], lay)
+    plan.stage_seeing_stf(tio["ws"], lay)
+    torch.cuda.synchronize()
+    seeing = v["seeing"].cpu().numpy()
+    xs = np.array([oracle_fit_on_gpu_stats(plan, v, spec.F, c, int(c)) for c in plan.cubes()])
+    assert np.allclose(seeing[:80], xs, rtol=FIT_TOL, atol=0)
+    assert seeing[80] == pytest.approx(1.0 / np.mean(1.0 / xs), rel=FIT_TOL)
+    # the estimate tracks the burst's seeing (D/r0 drawn in 8..15 per frame)
+    assert 5.0 < seeing[80] < 20.0
