@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--spectra", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="frame-spectra storage (precision sweep)")
+    ap.add_argument("--acc", default="plain", choices=["plain", "kahan"], help="bispectrum sums")
+    ap.add_argument("--phase", default="fp32", choices=["fp32", "fp64"], help="recursion arithmetic")
     ap.add_argument("--size", default=None,
                     help="WxH override (profiling a smaller case of the same kernels)")
     return ap.parse_args()
@@ -302,7 +306,12 @@ def main():
         spec = dataclasses.replace(spec, W=w, H=h)
     b = make_burst(spec, channel=1, burst=rank, device=f"cuda:{local}")
     F = spec.F
-    ch = Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=F)
+    from paper_1701_00581_gb300 import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_FP16, SM_FP32,
+                                        SM_PHASE_FP32, SM_PHASE_FP64)
+    modes = dict(spectra_prec={"fp32": SM_FP32, "fp16": SM_FP16, "bf16": SM_BF16}[args.spectra],
+                 acc_mode={"plain": SM_ACC_PLAIN, "kahan": SM_ACC_KAHAN}[args.acc],
+                 phase_prec={"fp32": SM_PHASE_FP32, "fp64": SM_PHASE_FP64}[args.phase])
+    ch = Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=F, **modes)
     plan = Plan(ch, device=local)
     info = plan.info
     n_sub = info["n_sub"]
@@ -432,11 +441,14 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "bursts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.spectra == "fp32" else f"{args.spectra} spectra, f32 arithmetic",
                 "data": "synthetic",
                 "config": {"workload": f"{args.workload} burst: {spec.W}x{spec.H}x{F} uint16, "
                                        f"{n_sub} subfields of {N}^2 at 50% overlap, |v|<={R}",
-                           "path": "plain per-burst stages, FP32 spectra and arithmetic",
+                           "path": "plain per-burst stages",
+                           "precision": f"spectra {args.spectra}, bispectrum sums {args.acc} fp32, "
+                                        f"recursion {args.phase}",
                            "seeing": "estimated from each burst (spectral ratio over the non-overlapping "
                                      f"{N}^2 cubes, {info['n_cubes']} cubes)",
                            "l2": "inputs larger than L2 (no flush)",

@@ -59,6 +59,14 @@ extern "C" {
 #define SM_U16 0          /* frame samples: uint16 counts                     */
 #define SM_F32 1          /* frame samples: float32                           */
 
+#define SM_ACC_PLAIN 0    /* bispectrum sums: FP32, one rounding per frame    */
+#define SM_ACC_KAHAN 1    /* bispectrum sums: FP32 compensated (Kahan); each
+                           * subfield streams its frames twice (half of the
+                           * offsets per pass), about 2.5x the time          */
+
+#define SM_PHASE_FP32 0   /* phase recursion arithmetic FP32, phasors stored FP64 */
+#define SM_PHASE_FP64 1   /* phase recursion arithmetic FP64 throughout       */
+
 /* ---- one camera channel ------------------------------------------------ */
 typedef struct {
     int    W, H;          /* frame size in px (Table 1: 2560x2160, 1024x1024)  */
@@ -71,6 +79,8 @@ typedef struct {
     int    phase_weight;  /* SM_W_BISPEC / SM_W_UNIT                           */
     double ck;            /* Korff constant of the model STF (e.g. 0.435)      */
     int    max_frames;    /* largest burst length F accepted (>= 1)            */
+    int    acc_mode;      /* SM_ACC_PLAIN / SM_ACC_KAHAN                       */
+    int    phase_prec;    /* SM_PHASE_FP32 / SM_PHASE_FP64                     */
 } sm_channel;
 
 /* ======================================================================== *

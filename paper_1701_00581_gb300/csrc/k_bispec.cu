@@ -99,11 +99,24 @@ __device__ __forceinline__ void cp_async16(unsigned smem_addr, const void* gmem,
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" :: "r"(smem_addr), "l"(gmem), "r"(bytes));
 }
 
-// One frame of the thread's 4 x 8 pairs from the staged rectangles.  FULL:
-// the warp owns a used pair in every offset column, so no column is tested.
-template <bool FULL>
+// acc += t with Kahan compensation (c carries the rounding error of the sum);
+// explicit round-to-nearest intrinsics keep the compiler from fusing or
+// reassociating the correction away.
+__device__ __forceinline__ void kahan_add(float& acc, float& c, float t) {
+    const float y = __fsub_rn(t, c);
+    const float s = __fadd_rn(acc, y);
+    c = __fsub_rn(__fsub_rn(s, acc), y);
+    acc = s;
+}
+
+// One frame of the thread's 4 targets x NC offset columns col0 .. col0+NC-1
+// from the staged rectangles; kkmask holds those columns' bits (bit k =
+// column col0 + k).  FULL: the warp owns a used pair in every one of them,
+// so no column is tested.  KAHAN: compensated sums.
+template <bool FULL, int NC, bool KAHAN>
 __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, int wyl, int gx, int warp,
-                                                 unsigned kkmask, float2 (&acc)[4][smi::VBX]) {
+                                                 unsigned kkmask, int col0, float2 (&acc)[4][NC],
+                                                 float2 (&comp)[4][KAHAN ? NC : 1]) {
     const float4* w4 = reinterpret_cast<const float4*>(Sb + OFF_W + wyl * PW + 4 * gx);
     const float4 w01 = w4[0], w23 = w4[1];
     const float2 a[4] = {make_float2(w01.x, -w01.y), make_float2(w01.z, -w01.w),   // conj I(w)
@@ -116,23 +129,28 @@ __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, 
         c[2 * q] = make_float2(t.x, t.y);
         c[2 * q + 1] = make_float2(t.z, t.w);
     }
-    const float4* v4 = reinterpret_cast<const float4*>(Sb + OFF_V + warp * smi::VBX);
+    const float4* v4 = reinterpret_cast<const float4*>(Sb + OFF_V + warp * smi::VBX + col0);
 #pragma unroll
-    for (int k2 = 0; k2 < smi::VBX / 2; ++k2) {
+    for (int k2 = 0; k2 < NC / 2; ++k2) {
         if (!FULL && !(kkmask & (3u << (2 * k2)))) continue;   // warp-uniform
-        const float4 bb = v4[k2];                               // I(v) for kk = 2 k2, 2 k2 + 1 (broadcast)
+        const float4 bb = v4[k2];                               // I(v) for two columns (broadcast)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int kk = 2 * k2 + e;
-            if (!FULL && !(kkmask & (1u << kk))) continue;      // warp-uniform
+            const int kl = 2 * k2 + e, kk = col0 + kl;
+            if (!FULL && !(kkmask & (1u << kl))) continue;      // warp-uniform
             const float2 b = e == 0 ? make_float2(bb.x, bb.y) : make_float2(bb.z, bb.w);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float2 u = c[j - kk + 7];
                 const float px = fmaf(u.x, b.x, -u.y * b.y);
                 const float py = fmaf(u.x, b.y, u.y * b.x);
-                acc[j][kk].x = fmaf(px, a[j].x, fmaf(-py, a[j].y, acc[j][kk].x));
-                acc[j][kk].y = fmaf(px, a[j].y, fmaf(py, a[j].x, acc[j][kk].y));
+                if constexpr (KAHAN) {
+                    kahan_add(acc[j][kl].x, comp[j][kl].x, fmaf(px, a[j].x, -py * a[j].y));
+                    kahan_add(acc[j][kl].y, comp[j][kl].y, fmaf(px, a[j].y, py * a[j].x));
+                } else {
+                    acc[j][kl].x = fmaf(px, a[j].x, fmaf(-py, a[j].y, acc[j][kl].x));
+                    acc[j][kl].y = fmaf(px, a[j].y, fmaf(py, a[j].x, acc[j][kl].y));
+                }
             }
         }
     }
@@ -177,8 +195,10 @@ __device__ __forceinline__ void chunk_copy(const PlanDev& p, int c, int wx0, int
     bytes = i0 < 0 ? 0 : (i1 >= 0 ? 16 : 8);
 }
 
-// VCH: V moves in 16-byte chunks (every tile's vx0 + K is even).
-template <int PREC, bool VCH>
+// VCH: V moves in 16-byte chunks (every tile's vx0 + K is even).  KAHAN:
+// compensated sums; the accumulators and their corrections fill the
+// registers of 4 columns, so the frames stream twice, 4 columns per pass.
+template <int PREC, bool VCH, bool KAHAN>
 __global__ void __launch_bounds__(THREADS, 4)
 k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict__ B) {
     constexpr bool ASYNC = Staging<PREC>::ASYNC;
@@ -202,16 +222,24 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
             mine |= pair_used(wx0 + 4 * gx + j, wy0 + wyl, vx0 + kk, vy0 + warp, p.r2i, p.R * p.R);
         if (__any_sync(0xffffffffu, mine)) kkmask |= 1u << kk;
     }
-    const bool active = kkmask != 0;
 
-    float2 acc[4][smi::VBX];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int kk = 0; kk < smi::VBX; ++kk) acc[j][kk] = make_float2(0.f, 0.f);
-
+    constexpr int NP = KAHAN ? 2 : 1;                // passes over the frames
+    constexpr int NC = smi::VBX / NP;                // offset columns per pass
     const size_t box = (size_t)p.box_rows * p.box_pitch;
     const size_t sbase = (size_t)sl * F * box;
+    float2* out = B + (size_t)(sl * p.n_tiles + tile) * TILE_PAIRS;
+    const float sc = 1.0f / (float)F;
+    auto write_out = [&](int col0, const float2 (&acc)[4][NC]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float4* o = reinterpret_cast<float4*>(out + (wyl * smi::WBX + 4 * gx + j) * TILE_V +
+                                                  warp * smi::VBX + col0);
+#pragma unroll
+            for (int q = 0; q < NC / 2; ++q)
+                o[q] = make_float4(acc[j][2 * q].x * sc, acc[j][2 * q].y * sc,
+                                   acc[j][2 * q + 1].x * sc, acc[j][2 * q + 1].y * sc);
+        }
+    };
     if (ASYNC) {
         const float2* sp = reinterpret_cast<const float2*>(spec) + sbase;
         const int nst = (F + FB - 1) / FB;
@@ -260,22 +288,40 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
             }
             asm volatile("cp.async.commit_group;");
         };
-        issue(0);
-        for (int st = 0; st < nst; ++st) {
-            asm volatile("cp.async.wait_group 0;");
-            __syncthreads();          // stage st visible to all; stage st-1 fully consumed
-            issue(st + 1);
-            if (!active) continue;
-            const float2* Sst = S + (st & 1) * FB * BUF;
-            if (kkmask == 0xffu) {
 #pragma unroll
-                for (int ff = 0; ff < FB; ++ff) accumulate_frame<true>(Sst + ff * BUF, wyl, gx, warp, kkmask, acc);
-            } else {
-#pragma unroll 1
-                for (int ff = 0; ff < FB; ++ff) accumulate_frame<false>(Sst + ff * BUF, wyl, gx, warp, kkmask, acc);
+        for (int pass = 0; pass < NP; ++pass) {
+            const int col0 = pass * NC;
+            const unsigned pm = (kkmask >> col0) & ((1u << NC) - 1u);
+            float2 acc[4][NC];
+            float2 comp[4][KAHAN ? NC : 1];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int k = 0; k < NC; ++k) acc[j][k] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < (KAHAN ? NC : 1); ++k) comp[j][k] = make_float2(0.f, 0.f);
             }
+            if (pass > 0) __syncthreads();             // the previous pass is done with the ring
+            issue(0);
+            for (int st = 0; st < nst; ++st) {
+                asm volatile("cp.async.wait_group 0;");
+                __syncthreads();          // stage st visible to all; stage st-1 fully consumed
+                issue(st + 1);
+                if (!pm) continue;
+                const float2* Sst = S + (st & 1) * FB * BUF;
+                if (pm == (1u << NC) - 1u) {
+#pragma unroll
+                    for (int ff = 0; ff < FB; ++ff)
+                        accumulate_frame<true, NC, KAHAN>(Sst + ff * BUF, wyl, gx, warp, pm, col0, acc, comp);
+                } else {
+#pragma unroll 1
+                    for (int ff = 0; ff < FB; ++ff)
+                        accumulate_frame<false, NC, KAHAN>(Sst + ff * BUF, wyl, gx, warp, pm, col0, acc, comp);
+                }
+            }
+            asm volatile("cp.async.wait_group 0;");
+            if (pm) write_out(col0, acc);
         }
-        asm volatile("cp.async.wait_group 0;");
     } else {
         // Which spectrum value each thread stages, and where it goes.
         int src[LPT], dst[LPT];
@@ -299,37 +345,40 @@ k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict
             dst[i] = d;
             src[i] = s;
         }
-        float2 pre[LPT];
 #pragma unroll
-        for (int i = 0; i < LPT; ++i)
-            pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, sbase + src[i]) : make_float2(0.f, 0.f);
-        for (int f = 0; f < F; ++f) {
-            float2* Sb = S + (f & 1) * BUF;
+        for (int pass = 0; pass < NP; ++pass) {
+            const int col0 = pass * NC;
+            const unsigned pm = (kkmask >> col0) & ((1u << NC) - 1u);
+            float2 acc[4][NC];
+            float2 comp[4][KAHAN ? NC : 1];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int k = 0; k < NC; ++k) acc[j][k] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < (KAHAN ? NC : 1); ++k) comp[j][k] = make_float2(0.f, 0.f);
+            }
+            if (pass > 0) __syncthreads();             // the previous pass is done with the buffers
+            float2 pre[LPT];
 #pragma unroll
             for (int i = 0; i < LPT; ++i)
-                if (dst[i] >= 0) Sb[dst[i]] = pre[i];
-            __syncthreads();
-            if (f + 1 < F) {
-                const size_t fb = sbase + (size_t)(f + 1) * box;
+                pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, sbase + src[i]) : make_float2(0.f, 0.f);
+            for (int f = 0; f < F; ++f) {
+                float2* Sb = S + (f & 1) * BUF;
 #pragma unroll
                 for (int i = 0; i < LPT; ++i)
-                    pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, fb + src[i]) : make_float2(0.f, 0.f);
+                    if (dst[i] >= 0) Sb[dst[i]] = pre[i];
+                __syncthreads();
+                if (f + 1 < F) {
+                    const size_t fb = sbase + (size_t)(f + 1) * box;
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i)
+                        pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, fb + src[i]) : make_float2(0.f, 0.f);
+                }
+                if (pm) accumulate_frame<false, NC, KAHAN>(Sb, wyl, gx, warp, pm, col0, acc, comp);
             }
-            if (active) accumulate_frame<false>(Sb, wyl, gx, warp, kkmask, acc);
+            if (pm) write_out(col0, acc);
         }
-    }
-
-    if (!active) return;
-    const float sc = 1.0f / (float)F;
-    float2* out = B + (size_t)(sl * p.n_tiles + tile) * TILE_PAIRS;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float4* o = reinterpret_cast<float4*>(out + (wyl * smi::WBX + 4 * gx + j) * TILE_V +
-                                              warp * smi::VBX);
-#pragma unroll
-        for (int q = 0; q < smi::VBX / 2; ++q)
-            o[q] = make_float4(acc[j][2 * q].x * sc, acc[j][2 * q].y * sc,
-                               acc[j][2 * q + 1].x * sc, acc[j][2 * q + 1].y * sc);
     }
 }
 
@@ -341,13 +390,22 @@ cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, in
                               cudaStream_t st) {
     dim3 grid(p.n_tiles, nsub);
     const bool vch = ((p.v_org + p.K) & 1) == 0;     // every tile's V starts at an even column
-    if (p.prec == SM_FP32) {
-        if (vch) k_bispectrum<SM_FP32, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
-        else k_bispectrum<SM_FP32, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+    if (p.acc_mode == SM_ACC_KAHAN) {
+        if (p.prec == SM_FP32) {
+            if (vch) k_bispectrum<SM_FP32, true, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+            else k_bispectrum<SM_FP32, false, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        } else if (p.prec == SM_FP16) {
+            k_bispectrum<SM_FP16, false, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        } else {
+            k_bispectrum<SM_BF16, false, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        }
+    } else if (p.prec == SM_FP32) {
+        if (vch) k_bispectrum<SM_FP32, true, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        else k_bispectrum<SM_FP32, false, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
     } else if (p.prec == SM_FP16) {
-        k_bispectrum<SM_FP16, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        k_bispectrum<SM_FP16, false, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
     } else {
-        k_bispectrum<SM_BF16, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        k_bispectrum<SM_BF16, false, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
     }
     return cudaGetLastError();
 }

@@ -10,9 +10,10 @@
 // flight together, and sum exp(i(phi(w-v) + phi(v))) conj B over the
 // offsets of the tile into one partial per item.  Then one warp per point
 // adds its partials along a fixed tree and stores z(w) = S / |S|: the
-// result does not depend on scheduling.  Arithmetic is FP32 (GB300's FP64
-// unit is shared by the SM's warps and a small fraction of its FP32 rate);
-// the known phasors live in shared memory and the result is stored as FP64.
+// result does not depend on scheduling.  Arithmetic is FP32 by default
+// (GB300's FP64 unit is shared by the SM's warps and a small fraction of its
+// FP32 rate), or FP64 throughout when the channel asks for it; the known
+// phasors live in shared memory in that type and the result is stored as FP64.
 #include "sm_internal.h"
 
 namespace {
@@ -24,11 +25,26 @@ using smi::TILE_V;
 constexpr int PH_THREADS = 512;
 constexpr int PH_WARPS = PH_THREADS / 32;
 
+// Complex values of the recursion's arithmetic type T.
+template <typename T> struct Cx;
+template <> struct Cx<float> {
+    using T2 = float2;
+    __device__ static float2 make(float x, float y) { return make_float2(x, y); }
+    __device__ static float rnorm(float n2) { return rsqrtf(n2); }
+};
+template <> struct Cx<double> {
+    using T2 = double2;
+    __device__ static double2 make(double x, double y) { return make_double2(x, y); }
+    __device__ static double rnorm(double n2) { return 1.0 / sqrt(n2); }
+};
+
 // z of any frequency from the half-box copy (row 0 holds both signs).
-__device__ __forceinline__ float2 zget(const float2* zs, int pitch, int K, int kx, int ky) {
+template <typename T2>
+__device__ __forceinline__ T2 zget(const T2* zs, int pitch, int K, int kx, int ky) {
     if (ky >= 0) return zs[ky * pitch + kx + K];
-    const float2 t = zs[(-ky) * pitch - kx + K];
-    return make_float2(t.x, -t.y);
+    T2 t = zs[(-ky) * pitch - kx + K];
+    t.y = -t.y;
+    return t;
 }
 
 constexpr int PH_ITEMS = 8;           // items per warp batch (all loads in flight together)
@@ -37,19 +53,20 @@ constexpr int PH_ITEMS = 8;           // items per warp batch (all loads in flig
 // exchanges at distances 16, 8 and 4 each lane holds one item's partial sum
 // over 8 lanes (item = lane >> 2), then two xor steps finish it.  18 shuffles
 // instead of 8 full reductions (80).
-__device__ __forceinline__ float2 reduce8(float2 (&s)[PH_ITEMS], int lane) {
+template <typename T2>
+__device__ __forceinline__ T2 reduce8(T2 (&s)[PH_ITEMS], int lane) {
 #pragma unroll
     for (int lvl = 0, o = 16, n = PH_ITEMS / 2; lvl < 3; ++lvl, o >>= 1, n >>= 1) {
         const bool hi = lane & o;
 #pragma unroll
         for (int q = 0; q < n; ++q) {
-            const float2 keep = hi ? s[q + n] : s[q];
-            const float2 give = hi ? s[q] : s[q + n];
+            const T2 keep = hi ? s[q + n] : s[q];
+            const T2 give = hi ? s[q] : s[q + n];
             s[q].x = keep.x + __shfl_xor_sync(0xffffffffu, give.x, o);
             s[q].y = keep.y + __shfl_xor_sync(0xffffffffu, give.y, o);
         }
     }
-    float2 r = s[0];
+    T2 r = s[0];
 #pragma unroll
     for (int o = 2; o > 0; o >>= 1) {
         r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
@@ -63,20 +80,15 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(sa), "l"(gmem));
 }
 
-// Shared memory: item partial sums of the ring, the phasor table, the item
-// records of the next ring and the point records of this and the next ring.
-struct PhaseSmem {
-    float2* part;   // [max_ring_items]
-    float2* zs;     // [hb]
-    int4* itm;      // [max_ring_items] items of ring r + 1
-    int4* prc;      // [2][max_ring_points] point records, by ring parity
-};
-__host__ __device__ inline size_t phase_layout(int hb_rows, int pitch, int mri, int mrp, size_t* o_zs,
+// Shared memory: item partial sums of the ring and the phasor table (complex
+// values of e2 bytes), the item records of the next ring and the point
+// records of this and the next ring.
+__host__ __device__ inline size_t phase_layout(int hb_rows, int pitch, int mri, int mrp, size_t e2, size_t* o_zs,
                                                size_t* o_itm, size_t* o_prc) {
     size_t o = 0;
-    o += ((size_t)mri * sizeof(float2) + 15) & ~(size_t)15;
+    o += ((size_t)mri * e2 + 15) & ~(size_t)15;
     *o_zs = o;
-    o += ((size_t)hb_rows * pitch * sizeof(float2) + 15) & ~(size_t)15;
+    o += ((size_t)hb_rows * pitch * e2 + 15) & ~(size_t)15;
     *o_itm = o;
     o += (size_t)mri * sizeof(int4);
     *o_prc = o;
@@ -84,24 +96,26 @@ __host__ __device__ inline size_t phase_layout(int hb_rows, int pitch, int mri, 
     return o;
 }
 
-__global__ void __launch_bounds__(PH_THREADS, 2)
+template <typename T>
+__global__ void __launch_bounds__(PH_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         double2* __restrict__ z) {
+    using T2 = typename Cx<T>::T2;
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K, pitch = p.box_pitch;
     const size_t hb = (size_t)p.hb_rows * pitch;
     size_t o_zs, o_itm, o_prc;
-    phase_layout(p.hb_rows, pitch, p.max_ring_items, p.max_ring_points, &o_zs, &o_itm, &o_prc);
-    PhaseSmem sm{reinterpret_cast<float2*>(smem), reinterpret_cast<float2*>(smem + o_zs),
-                 reinterpret_cast<int4*>(smem + o_itm), reinterpret_cast<int4*>(smem + o_prc)};
-    float2* part = sm.part;
-    float2* zs = sm.zs;
+    phase_layout(p.hb_rows, pitch, p.max_ring_items, p.max_ring_points, sizeof(T2), &o_zs, &o_itm, &o_prc);
+    T2* part = reinterpret_cast<T2*>(smem);
+    T2* zs = reinterpret_cast<T2*>(smem + o_zs);
+    int4* const itm = reinterpret_cast<int4*>(smem + o_itm);
+    int4* const prc = reinterpret_cast<int4*>(smem + o_prc);
     const int sl = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     double2* zo = z + (size_t)sl * hb;
-    for (int e = tid; e < (int)hb; e += PH_THREADS) zs[e] = make_float2(0.f, 0.f);
+    for (int e = tid; e < (int)hb; e += PH_THREADS) zs[e] = Cx<T>::make(0, 0);
     __syncthreads();
     if (tid == 0) {
-        zs[K] = make_float2(1.f, 0.f);
+        zs[K] = Cx<T>::make(1, 0);
         zo[K] = make_double2(1.0, 0.0);
         // anchors: z(e_x) = M(e_x)/|M(e_x)|, z(e_y) = M(e_y)/|M(e_y)|
         const float2 mx = M[(size_t)sl * hb + K + 1];
@@ -110,9 +124,9 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         const double2 ax = n > 0 ? make_double2(mx.x / n, mx.y / n) : make_double2(1.0, 0.0);
         n = hypot((double)my.x, (double)my.y);
         const double2 ay = n > 0 ? make_double2(my.x / n, my.y / n) : make_double2(1.0, 0.0);
-        zs[K + 1] = make_float2((float)ax.x, (float)ax.y);
-        zs[K - 1] = make_float2((float)ax.x, -(float)ax.y);
-        zs[pitch + K] = make_float2((float)ay.x, (float)ay.y);
+        zs[K + 1] = Cx<T>::make((T)ax.x, (T)ax.y);
+        zs[K - 1] = Cx<T>::make((T)ax.x, -(T)ax.y);
+        zs[pitch + K] = Cx<T>::make((T)ay.x, (T)ay.y);
         zo[K + 1] = ax;
         zo[K - 1] = make_double2(ax.x, -ax.y);
         zo[pitch + K] = ay;
@@ -126,8 +140,8 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         if (q < p.n_rings) {
             const int i0 = p.ring_items[q], ni = p.ring_items[q + 1] - i0;
             const int p0 = p.ring_start[q], np = p.ring_start[q + 1] - p0;
-            for (int e = tid; e < ni; e += PH_THREADS) cp_async16(sm.itm + e, p.items + i0 + e);
-            int4* pr = sm.prc + (q & 1) * p.max_ring_points;
+            for (int e = tid; e < ni; e += PH_THREADS) cp_async16(itm + e, p.items + i0 + e);
+            int4* pr = prc + (q & 1) * p.max_ring_points;
             for (int e = tid; e < np; e += PH_THREADS) cp_async16(pr + e, p.point_rec + p0 + e);
         }
         asm volatile("cp.async.commit_group;");
@@ -163,7 +177,7 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
     stage(0);
     asm volatile("cp.async.wait_group 0;");
     __syncthreads();                              // anchors and ring 0 records visible
-    load_batch(sm.itm, warp, ni);
+    load_batch(itm, warp, ni);
     __syncthreads();                              // staging buffer free again
     for (int r = 0; r < p.n_rings; ++r) {
         const bool more = r + 1 < p.n_rings;
@@ -171,52 +185,52 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         const int nin = more ? p.ring_items[r + 2] - i0n : 0;
         const int npn = more ? p.ring_start[r + 2] - p.ring_start[r + 1] : 0;
         stage(r + 1);
-        // (1) items: FP32 products, one term per lane, FP32 item sums
+        // (1) items: products in T, one term per lane, item sums in T
         for (int base = warp; base < ni; base += PH_WARPS * PH_ITEMS) {
             if (base != warp) load_batch(p.items + i0, base, ni);
-            float2 t[PH_ITEMS];
+            T2 t[PH_ITEMS];
 #pragma unroll
             for (int q = 0; q < PH_ITEMS; ++q) {
-                t[q] = make_float2(0.f, 0.f);
+                t[q] = Cx<T>::make(0, 0);
                 if (okm & (1u << q)) {
                     const int wx = (signed char)(pk[q] & 255), wy = (signed char)((pk[q] >> 8) & 255);
                     const int vx = (signed char)((pk[q] >> 16) & 255) + (lane % smi::VBX);
                     const int vy = (signed char)((pk[q] >> 24) & 255) + (lane / smi::VBX);
-                    const float2 b = bv[q];
-                    const float2 zu = zget(zs, pitch, K, wx - vx, wy - vy);
-                    const float2 zv = zget(zs, pitch, K, vx, vy);
-                    const float2 c = make_float2(zu.x * zv.x - zu.y * zv.y, zu.x * zv.y + zu.y * zv.x);
-                    float tx = c.x * b.x + c.y * b.y;      // c * conj(b)
-                    float ty = c.y * b.x - c.x * b.y;
+                    const T bx = (T)bv[q].x, by = (T)bv[q].y;
+                    const T2 zu = zget(zs, pitch, K, wx - vx, wy - vy);
+                    const T2 zv = zget(zs, pitch, K, vx, vy);
+                    const T2 c = Cx<T>::make(zu.x * zv.x - zu.y * zv.y, zu.x * zv.y + zu.y * zv.x);
+                    T tx = c.x * bx + c.y * by;            // c * conj(b)
+                    T ty = c.y * bx - c.x * by;
                     if (unit) {
-                        const float m = sqrtf(b.x * b.x + b.y * b.y);
-                        if (m > 0.f) {
+                        const T m = sqrt(bx * bx + by * by);
+                        if (m > (T)0) {
                             tx /= m;
                             ty /= m;
                         } else {
-                            tx = ty = 0.f;
+                            tx = ty = (T)0;
                         }
                     }
-                    t[q] = make_float2(tx, ty);
+                    t[q] = Cx<T>::make(tx, ty);
                 }
             }
-            const float2 sum = reduce8(t, lane);
+            const T2 sum = reduce8(t, lane);
             const int e = base + (lane >> 2) * PH_WARPS;
             if ((lane & 3) == 0 && e < ni) part[e] = sum;
         }
         asm volatile("cp.async.wait_group 0;");
         __syncthreads();                          // partials complete, ring r+1 records visible
-        if (more) load_batch(sm.itm, warp, nin);
+        if (more) load_batch(itm, warp, nin);
         // (3) one warp per point: sum of its items along a fixed shuffle
-        // tree, then z = S / |S|.  FP32: the phasors feed the next rings in
-        // FP32 anyway, and GB300's shared FP64 unit serialised this step
-        // across warps when it ran in FP64.  The stored state is FP64.
-        const int4* pr = sm.prc + (r & 1) * p.max_ring_points;
+        // tree, then z = S / |S|, in T (with T = float GB300's shared FP64
+        // unit no longer serialises this step across warps).  The stored
+        // state is FP64.
+        const int4* pr = prc + (r & 1) * p.max_ring_points;
         for (int pl = warp; pl < np; pl += PH_WARPS) {
             const int4 rec = pr[pl];
-            float sx = 0.f, sy = 0.f;
+            T sx = 0, sy = 0;
             for (int a = rec.z + lane; a < rec.w; a += 32) {
-                const float2 v = part[a];
+                const T2 v = part[a];
                 sx += v.x;
                 sy += v.y;
             }
@@ -226,17 +240,17 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
             }
             if (lane == 0) {
-                const float n2 = sx * sx + sy * sy;
-                float2 zz = make_float2(1.f, 0.f);
-                if (n2 > 0.f) {
-                    const float inv = rsqrtf(n2);
-                    zz = make_float2(sx * inv, sy * inv);
+                const T n2 = sx * sx + sy * sy;
+                T2 zz = Cx<T>::make(1, 0);
+                if (n2 > (T)0) {
+                    const T inv = Cx<T>::rnorm(n2);
+                    zz = Cx<T>::make(sx * inv, sy * inv);
                 }
                 const int o = rec.y * pitch + rec.x + K;
                 zs[o] = zz;
                 zo[o] = make_double2((double)zz.x, (double)zz.y);
                 if (rec.y == 0) {
-                    zs[-rec.x + K] = make_float2(zz.x, -zz.y);
+                    zs[-rec.x + K] = Cx<T>::make(zz.x, -zz.y);
                     zo[-rec.x + K] = make_double2((double)zz.x, -(double)zz.y);
                 }
             }
@@ -252,17 +266,24 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
 
 namespace smk {
 
-size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_ring_points) {
+size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_ring_points, int phase_prec) {
     size_t a, b, c;
-    return phase_layout(hb_rows, box_pitch, max_ring_items, max_ring_points, &a, &b, &c);
+    return phase_layout(hb_rows, box_pitch, max_ring_items, max_ring_points,
+                        phase_prec == SM_PHASE_FP64 ? sizeof(double2) : sizeof(float2), &a, &b, &c);
 }
 
 cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M,
                          double2* z, cudaStream_t st) {
-    const size_t sm = phase_smem_bytes(p.hb_rows, p.box_pitch, p.max_ring_items, p.max_ring_points);
-    cudaError_t e = cudaFuncSetAttribute(k_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_phase<<<nsub, PH_THREADS, sm, st>>>(p, B, M, z);
+    const size_t sm = phase_smem_bytes(p.hb_rows, p.box_pitch, p.max_ring_items, p.max_ring_points, p.phase_prec);
+    if (p.phase_prec == SM_PHASE_FP64) {
+        cudaError_t e = cudaFuncSetAttribute(k_phase<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_phase<double><<<nsub, PH_THREADS, sm, st>>>(p, B, M, z);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_phase<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_phase<float><<<nsub, PH_THREADS, sm, st>>>(p, B, M, z);
+    }
     return cudaGetLastError();
 }
 

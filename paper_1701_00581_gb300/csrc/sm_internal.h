@@ -38,6 +38,7 @@ struct PlanDev {
     int v_org;               // x origin of the offset-block grid (odd: -R, or -R - 7 for even R),
                              //   so that every difference rectangle starts at an even box column
     int prec, weight;
+    int acc_mode, phase_prec;
     const int4* subs;        // [n_sub] x0, y0, w, h
     const float* winx;       // [n_sub][N] window along x (0 beyond the extent)
     const float* winy;       // [n_sub][N]
@@ -94,5 +95,6 @@ cudaError_t launch_inverse(const smi::PlanDev& p, int F, int sub0, int nsub, con
 cudaError_t launch_mosaic(const smi::PlanDev& p, const float* rec, float* out, uint8_t* valid,
                           cudaStream_t st);
 size_t spectra_smem_bytes(int N, int K);
-size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_ring_points);
+size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_ring_points,
+                        int phase_prec);
 }  // namespace smk

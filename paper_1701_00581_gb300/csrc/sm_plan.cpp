@@ -68,12 +68,18 @@ int validate_channel(const sm_channel* ch) {
         set_error("phase_weight must be SM_W_BISPEC or SM_W_UNIT"); return SM_EINVAL;
     }
     if (ch->max_frames < 1) { set_error("max_frames must be >= 1"); return SM_EINVAL; }
+    if (ch->acc_mode != SM_ACC_PLAIN && ch->acc_mode != SM_ACC_KAHAN) {
+        set_error("acc_mode must be SM_ACC_PLAIN or SM_ACC_KAHAN"); return SM_EINVAL;
+    }
+    if (ch->phase_prec != SM_PHASE_FP32 && ch->phase_prec != SM_PHASE_FP64) {
+        set_error("phase_prec must be SM_PHASE_FP32 or SM_PHASE_FP64"); return SM_EINVAL;
+    }
     if (!(ch->ck >= 0.0)) { set_error("ck must be >= 0"); return SM_EINVAL; }
     if (smk::spectra_smem_bytes(ch->N, K) > 227 * 1024) {
         set_error("fc*N too large for the shared-memory FFT at this N"); return SM_EINVAL;
     }
     const int pitch = ((2 * K + 1) + 3) / 4 * 4;
-    if (smk::phase_smem_bytes(K + 1, pitch, 0, 0) > 200 * 1024) {
+    if (smk::phase_smem_bytes(K + 1, pitch, 0, 0, ch->phase_prec) > 200 * 1024) {
         set_error("phase table exceeds shared memory"); return SM_EINVAL;
     }
     return SM_OK;
@@ -107,6 +113,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.logN = N == 64 ? 6 : (N == 128 ? 7 : 8);
     d.r2i = r2i;
     d.prec = ch->spectra_prec; d.weight = ch->phase_weight;
+    d.acc_mode = ch->acc_mode; d.phase_prec = ch->phase_prec;
     d.box_rows = K + R + 1;
     d.box_cols = 2 * K + 1;
     d.box_pitch = (d.box_cols + 3) / 4 * 4;
@@ -314,7 +321,8 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
             pl->point_rec[pi] = make_int4(pts[pi].x, pts[pi].y, pl->point_items[pi] - pl->ring_items[rr],
                                           pl->point_items[pi + 1] - pl->ring_items[rr]);
     }
-    if (smk::phase_smem_bytes(d.hb_rows, d.box_pitch, d.max_ring_items, d.max_ring_points) > 227 * 1024) {
+    if (smk::phase_smem_bytes(d.hb_rows, d.box_pitch, d.max_ring_items, d.max_ring_points, d.phase_prec) >
+        227 * 1024) {
         delete pl;
         set_error("phase recursion tables exceed shared memory");
         return SM_EINVAL;
