@@ -30,7 +30,9 @@ stated in each docstring:
 * modulus (Sect. 3.2, Eq. 1) with a model STF (Sect. 3.2), filtered by the
   diffraction OTF T0;
 * recursive phase (Sect. 3.2; LWW 1983), rings of equal |w|^2, anchors from
-  the burst-mean spectrum, |B| weighting by default;
+  the burst-mean spectrum, |B| weighting by default (unit and SNR weights
+  as options), optionally refined by least-squares sweeps (the "or
+  iteratively" of the method);
 * inverse DFT, flux rescale and the mean restored under the window
   (Sect. 2, Sect. 3.2), mosaic as
   sum(rec) / sum(window) (Sect. 3.2, the merge step).
@@ -49,6 +51,7 @@ import numpy as np
 
 W_BISPEC = 0     # phasor terms weighted by |B| (the plain sum of B's phasors)
 W_UNIT = 1       # unit-modulus phasor terms
+W_SNR = 2        # terms weighted by |B| / (P(u) P(v) P(w)), i.e. |B|^2 over its speckle-noise variance
 
 
 # ----------------------------------------------------------------------------
@@ -469,8 +472,29 @@ def recursion_rings(N: int, fc: float) -> List[np.ndarray]:
     return rings
 
 
+def _term_weight(b: np.ndarray, weight: int, P: Optional[np.ndarray], pu, pv, pw) -> np.ndarray:
+    """Factor multiplying the |B|-weighted phasor term z(u) z(v) conj B of each split.
+
+    W_BISPEC: 1.  W_UNIT: 1/|B| (0 where B = 0).  W_SNR: 1 / (P(u) P(v) P(w)):
+    the speckle-noise variance of the mean bispectrum is about
+    P(u) P(v) P(u+v) / F (Wirnitzer 1985), so the term is weighted by
+    |B|^2 / variance (0 where the product is not positive).
+    """
+    if weight == W_BISPEC:
+        return np.ones(len(b))
+    if weight == W_UNIT:
+        mag = np.abs(b)
+        return np.where(mag > 0, 1.0 / np.where(mag > 0, mag, 1.0), 0.0)
+    if weight == W_SNR:
+        if P is None:
+            raise ValueError("SNR weighting needs the power spectrum P")
+        den = pu * pv * pw
+        return np.where(den > 0, 1.0 / np.where(den > 0, den, 1.0), 0.0)
+    raise ValueError("unknown weighting")
+
+
 def phase_recursion(B: np.ndarray, pairs: np.ndarray, M: np.ndarray, N: int, fc: float,
-                    R: int, weight: int = W_BISPEC) -> np.ndarray:
+                    R: int, weight: int = W_BISPEC, P: Optional[np.ndarray] = None) -> np.ndarray:
     """Unit phasors z(k) = exp(i phi(k)) of the object on the centred grid.
 
     Speckle masking (Sect. 2, Sect. 3.2): arg B(u, v) = phi(u) + phi(v) -
@@ -483,7 +507,8 @@ def phase_recursion(B: np.ndarray, pairs: np.ndarray, M: np.ndarray, N: int, fc:
     * the phasor of w sums exp(i(phi(u) + phi(v))) conj B(u, v) over
       v with 0 < |v| <= R, u = w - v, |u|^2 < |w|^2, |v|^2 < |w|^2, reading
       B(u, v) = conj B(-u, -v) when u is in the lower half plane;
-      ``W_UNIT`` divides each term by |B| (terms with B = 0 dropped);
+      ``W_UNIT`` divides each term by |B| (terms with B = 0 dropped),
+      ``W_SNR`` divides it by P(u) P(v) P(w) (``_term_weight``);
     * z(w) = phasor / |phasor|, and z(w) = 1 when the phasor is 0;
     * z(-w) = conj z(w).
     """
@@ -526,14 +551,83 @@ def phase_recursion(B: np.ndarray, pairs: np.ndarray, M: np.ndarray, N: int, fc:
             if not (known[uy + c, ux + c].all() and known[vy + c, vx + c].all()):
                 raise AssertionError("recursion used an unknown phase")
             terms = z[uy + c, ux + c] * z[vy + c, vx + c] * np.conj(b)
-            if weight == W_UNIT:
-                mag = np.abs(b)
-                keep = mag > 0
-                terms = terms[keep] / mag[keep]
+            if weight != W_BISPEC:
+                pu = P[uy + c, ux + c] if P is not None else None
+                pv = P[vy + c, vx + c] if P is not None else None
+                pw = P[wy + c, wx + c] if P is not None else None
+                terms = terms * _term_weight(b, weight, P, pu, pv, pw)
             s = terms.sum()
             vals.append(s / abs(s) if abs(s) > 0 else 1.0 + 0j)
         for (wx, wy), val in zip(ring, vals):
             setz(int(wx), int(wy), val)
+    return z
+
+
+def recursion_splits(N: int, fc: float, R: int) -> np.ndarray:
+    """Every split (w, v) the recursion reads, as (wx, wy, vx, vy): w in H with
+    2 <= |w|^2 <= r^2, v in V, |w - v| < |w| and |v| < |w|."""
+    out = []
+    V = domain_V(R)
+    v2 = V[:, 0] ** 2 + V[:, 1] ** 2
+    for ring in recursion_rings(N, fc):
+        for (wx, wy) in ring:
+            w2 = wx * wx + wy * wy
+            ok = ((wx - V[:, 0]) ** 2 + (wy - V[:, 1]) ** 2 < w2) & (v2 < w2)
+            for vx, vy in V[ok]:
+                out.append((wx, wy, vx, vy))
+    return np.array(out, dtype=np.int64).reshape(-1, 4)
+
+
+def phase_refine(z: np.ndarray, B: np.ndarray, pairs: np.ndarray, N: int, fc: float, R: int,
+                 weight: int = W_BISPEC, P: Optional[np.ndarray] = None, iters: int = 1) -> np.ndarray:
+    """Iterative (least-squares) phase from the bispectrum, started from the recursion.
+
+    The recursion uses each split w = u + v only to estimate phi(w).  Read as
+    one least-squares problem, every split constrains all three phases:
+    maximise  J(z) = sum over splits of  g * Re[conj B(u, v) z(u) z(v) conj z(w)]
+    over unit phasors z (g the weighting factor of the recursion's terms).
+    With the other phases fixed, J is largest at z(k) = S_k / |S_k| where
+    S_k sums  g z(u) z(v) conj B  over the splits with w = k,
+    g z(w) conj z(v) B  over those with u = k  and  g z(w) conj z(u) B  over
+    those with v = k (z(-k) = conj z(k) folds lower-half occurrences onto k).
+    One Jacobi sweep applies that update to every recursion point at once
+    from the previous sweep's phases; the anchors (0, +-e_x, +-e_y) stay
+    fixed, and a point whose S_k vanishes keeps its phase.  The paper names
+    the option ("or iteratively") without details; this is our reading.
+    """
+    r = cutoff_radius(N, fc)
+    K = int(math.floor(r))
+    c = N // 2
+    idx = _PairIndex(pairs, K, R)
+    sp = recursion_splits(N, fc, R)
+    wx, wy, vx, vy = sp.T
+    ux, uy = wx - vx, wy - vy
+    up = in_half_plane(ux, uy)
+    b = np.empty(len(sp), dtype=np.complex128)
+    b[up] = B[idx.find(ux[up], uy[up], vx[up], vy[up])]
+    b[~up] = np.conj(B[idx.find(-ux[~up], -uy[~up], -vx[~up], -vy[~up])])
+    g = _term_weight(b, weight, P,
+                     P[uy + c, ux + c] if P is not None else None,
+                     P[vy + c, vx + c] if P is not None else None,
+                     P[wy + c, wx + c] if P is not None else None)
+    pts = np.concatenate(recursion_rings(N, fc))
+    z = z.copy()
+    for _ in range(iters):
+        zu, zv, zw = z[uy + c, ux + c], z[vy + c, vx + c], z[wy + c, wx + c]
+        S = np.zeros((N, N), dtype=np.complex128)
+        for (kx, ky, t) in ((wx, wy, g * zu * zv * np.conj(b)),
+                            (ux, uy, g * zw * np.conj(zv) * b),
+                            (vx, vy, g * zw * np.conj(zu) * b)):
+            h = in_half_plane(kx, ky)
+            np.add.at(S, (ky[h] + c, kx[h] + c), t[h])
+            np.add.at(S, (-ky[~h] + c, -kx[~h] + c), np.conj(t[~h]))
+        new = z.copy()
+        for (px, py) in pts:
+            sk = S[py + c, px + c]
+            if abs(sk) > 0:
+                new[py + c, px + c] = sk / abs(sk)
+                new[-py + c, -px + c] = np.conj(sk / abs(sk))
+        z = new
     return z
 
 
@@ -582,8 +676,10 @@ def mosaic(recs: Sequence[np.ndarray], subs: Sequence[Tuple[int, int, int, int]]
 # ----------------------------------------------------------------------------
 def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: int,
                          fc: float, R: int, taper: int, stf: np.ndarray,
-                         weight: int = W_BISPEC, pairs: Optional[np.ndarray] = None) -> Dict:
-    """All steps for one subfield; returns every intermediate."""
+                         weight: int = W_BISPEC, pairs: Optional[np.ndarray] = None,
+                         iters: int = 0) -> Dict:
+    """All steps for one subfield; returns every intermediate.  ``iters``
+    least-squares sweeps (``phase_refine``) follow the recursion."""
     In, flux, mu = frame_spectra(frames, sub, N, taper)
     P, M = power_mean(In)
     noise = noise_floor(P, N, fc)
@@ -591,7 +687,9 @@ def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: 
         pairs = pair_domain(N, fc, R)
     B = bispectrum(In, pairs)
     A = amplitude(P, noise, stf, N, fc)
-    z = phase_recursion(B, pairs, M, N, fc, R, weight)
+    z = phase_recursion(B, pairs, M, N, fc, R, weight, P)
+    if iters > 0:
+        z = phase_refine(z, B, pairs, N, fc, R, weight, P, iters)
     rec = inverse(A, z, float(flux.mean()), float(mu.mean()), window2d(sub[2], sub[3], taper))
     return {"In": In, "flux": flux, "mu": mu, "P": P, "M": M, "noise": noise, "pairs": pairs,
             "B": B, "A": A, "z": z, "rec": rec}
@@ -599,7 +697,8 @@ def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: 
 
 def reconstruct_burst(frames: np.ndarray, N: int, stride: int, fc: float, R: int, taper: int,
                       stf: Optional[np.ndarray], weight: int = W_BISPEC,
-                      subfields: Optional[Sequence[int]] = None, ck: float = 0.435) -> Dict:
+                      subfields: Optional[Sequence[int]] = None, ck: float = 0.435,
+                      iters: int = 0) -> Dict:
     """Whole burst: every subfield (or the listed ones), then the mosaic.
 
     With ``stf`` None the STF is the model at the seeing estimated from the
@@ -613,7 +712,7 @@ def reconstruct_burst(frames: np.ndarray, N: int, stride: int, fc: float, R: int
     subs = subfield_grid(W, H, N, stride)
     pairs = pair_domain(N, fc, R)
     pick = range(len(subs)) if subfields is None else subfields
-    results = {s: reconstruct_subfield(frames, subs[s], N, fc, R, taper, stf, weight, pairs)
+    results = {s: reconstruct_subfield(frames, subs[s], N, fc, R, taper, stf, weight, pairs, iters)
                for s in pick}
     out = valid = None
     if subfields is None:
