@@ -56,6 +56,8 @@ def parse():
                     help="frame-spectra storage (precision sweep)")
     ap.add_argument("--acc", default="plain", choices=["plain", "kahan"], help="bispectrum sums")
     ap.add_argument("--phase", default="fp32", choices=["fp32", "fp64"], help="recursion arithmetic")
+    ap.add_argument("--weight", default="bispec", choices=["bispec", "unit", "snr"], help="phase-term weighting")
+    ap.add_argument("--iters", type=int, default=0, help="least-squares phase sweeps after the recursion")
     ap.add_argument("--size", default=None,
                     help="WxH override (profiling a smaller case of the same kernels)")
     return ap.parse_args()
@@ -307,10 +309,12 @@ def main():
     b = make_burst(spec, channel=1, burst=rank, device=f"cuda:{local}")
     F = spec.F
     from paper_1701_00581_gb300 import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_FP16, SM_FP32,
-                                        SM_PHASE_FP32, SM_PHASE_FP64)
+                                        SM_PHASE_FP32, SM_PHASE_FP64, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT)
     modes = dict(spectra_prec={"fp32": SM_FP32, "fp16": SM_FP16, "bf16": SM_BF16}[args.spectra],
                  acc_mode={"plain": SM_ACC_PLAIN, "kahan": SM_ACC_KAHAN}[args.acc],
-                 phase_prec={"fp32": SM_PHASE_FP32, "fp64": SM_PHASE_FP64}[args.phase])
+                 phase_prec={"fp32": SM_PHASE_FP32, "fp64": SM_PHASE_FP64}[args.phase],
+                 phase_weight={"bispec": SM_W_BISPEC, "unit": SM_W_UNIT, "snr": SM_W_SNR}[args.weight],
+                 phase_iters=args.iters)
     ch = Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=F, **modes)
     plan = Plan(ch, device=local)
     info = plan.info
@@ -338,7 +342,7 @@ def main():
         plan.stage_inverse(F, 0, n_sub, ws, lay, stream)
         plan.stage_mosaic(ws, lay, out, valid, stream)
 
-    launches_per_step = 9
+    launches_per_step = 9 + 2 * args.iters
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -382,6 +386,34 @@ def main():
                 "note": (f"{FLOPS_PER_TRIPLE} flops x {triples:.3e} used triples per launch; peak = "
                          f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                          f"{sm_max:.0f} MHz")}
+
+    # plain end to end: one burst at a time through sm_reconstruct, the
+    # frames copied in from pinned host memory and the mosaic copied out
+    # inside the timed region, nothing overlapped (the served path's baseline)
+    plain_e2e = None
+    if not args.no_e2e:
+        host_frames = torch.from_numpy(b["frames"]).pin_memory()
+        host_out = torch.empty((spec.H, spec.W), dtype=torch.float32).pin_memory()
+        dframes = torch.empty_like(frames)
+
+        def plain_one():
+            dframes.copy_(host_frames, non_blocking=True)
+            plan.reconstruct(dframes, F, None, n_sub, ws, lay, out, None, stream)
+            host_out.copy_(out, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(max(1, args.warmup)):
+            plain_one()
+        if world > 1:
+            dist.barrier()
+        t_p = time.perf_counter()
+        for _ in range(args.steps):
+            plain_one()
+        el_p = max_over_ranks(time.perf_counter() - t_p, dev)
+        plain_e2e = {"value": whole_job_rate(args.steps, world, el_p), "unit": "bursts/s",
+                     "h2d_bytes_per_step": int(b["frames"].nbytes), "d2h_bytes_per_step": int(spec.W * spec.H * 4),
+                     "note": "sm_reconstruct one burst at a time, copies not overlapped"}
+        del dframes, host_frames
 
     # end to end through the serving API, host buffers, copies inside the timed region
     e2e = None
@@ -449,12 +481,14 @@ def main():
                            "path": "plain per-burst stages",
                            "precision": f"spectra {args.spectra}, bispectrum sums {args.acc} fp32, "
                                         f"recursion {args.phase}",
+                           "phase": f"recursion weighted by {args.weight}"
+                                    + (f", {args.iters} least-squares sweeps" if args.iters else ""),
                            "seeing": "estimated from each burst (spectral ratio over the non-overlapping "
                                      f"{N}^2 cubes, {info['n_cubes']} cubes)",
                            "l2": "inputs larger than L2 (no flush)",
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": launches_per_step * args.steps,
-                "roofline": roofline, "clocks": clocks, "e2e": e2e, "serving": serving,
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "plain_e2e": plain_e2e, "serving": serving,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -55,6 +55,8 @@ extern "C" {
 
 #define SM_W_BISPEC 0     /* phase terms weighted by |B| (plain phasor sum)   */
 #define SM_W_UNIT   1     /* unit-modulus phase terms                         */
+#define SM_W_SNR    2     /* terms weighted by |B| / (P(u) P(v) P(w)): |B|^2
+                           * over the speckle-noise variance of B            */
 
 #define SM_U16 0          /* frame samples: uint16 counts                     */
 #define SM_F32 1          /* frame samples: float32                           */
@@ -81,6 +83,8 @@ typedef struct {
     int    max_frames;    /* largest burst length F accepted (>= 1)            */
     int    acc_mode;      /* SM_ACC_PLAIN / SM_ACC_KAHAN                       */
     int    phase_prec;    /* SM_PHASE_FP32 / SM_PHASE_FP64                     */
+    int    phase_iters;   /* least-squares sweeps after the recursion (0..64);
+                           * see sm_stage_phase                               */
 } sm_channel;
 
 /* ======================================================================== *
@@ -148,6 +152,8 @@ typedef struct {
     size_t seeing; /* [n_cubes + 1] double: D/r0 of every seeing cube, then the
                     * burst's D / mean r0                                    */
     size_t stf;    /* [N][N] double, centred: model STF at the burst's seeing */
+    size_t refine; /* [nsub][n_tiles][413] float2: least-squares sweep partials
+                    * (0 bytes when the channel's phase_iters is 0)         */
     size_t bytes;  /* total workspace size                                    */
 } sm_workspace_layout;
 
@@ -202,7 +208,16 @@ int sm_stage_bispectrum(const sm_plan* plan, int F, int nsub, void* ws,
                         const sm_workspace_layout* lay, void* stream);
 
 /* Sect. 3.2 (LWW recursion): unit phasors z on the half box, ring by ring
- * from the anchors z(e_x), z(e_y) = M/|M|.                                  */
+ * from the anchors z(e_x), z(e_y) = M/|M|; each point sums
+ * z(w-v) z(v) conj B(w-v, v) times the channel's weighting (1, 1/|B|, or
+ * 1/(P(w-v) P(v) P(w))).  With phase_iters > 0, that many least-squares
+ * sweeps follow ("or iteratively"): every split w = u + v then updates all
+ * three of its phases, z(k) = S_k / |S_k| with
+ * S_k = sum_{w=k} g z(u) z(v) conj B + sum_{u=k} g z(w) conj z(v) B
+ *     + sum_{v=k} g z(w) conj z(u) B   (g the weighting factor),
+ * from the previous sweep's phases (Jacobi), anchors fixed, a point with
+ * S_k = 0 keeping its phase.  The sweeps use a workspace buffer of
+ * 413 complex partial sums per bispectrum tile.                             */
 int sm_stage_phase(const sm_plan* plan, int nsub, void* ws,
                    const sm_workspace_layout* lay, void* stream);
 

@@ -16,7 +16,7 @@ SM_OK, SM_PENDING = 0, 1
 SM_EINVAL, SM_ENOMEM, SM_EBUSY, SM_ETIMEDOUT, SM_ECUDA, SM_ECANCELED, SM_ENOTFOUND = (
     -1, -2, -3, -4, -5, -6, -7)
 SM_FP32, SM_FP16, SM_BF16 = 0, 1, 2
-SM_W_BISPEC, SM_W_UNIT = 0, 1
+SM_W_BISPEC, SM_W_UNIT, SM_W_SNR = 0, 1, 2
 SM_U16, SM_F32 = 0, 1
 SM_ACC_PLAIN, SM_ACC_KAHAN = 0, 1
 SM_PHASE_FP32, SM_PHASE_FP64 = 0, 1
@@ -26,7 +26,7 @@ class sm_channel(C.Structure):
     _fields_ = [("W", C.c_int), ("H", C.c_int), ("N", C.c_int), ("stride", C.c_int), ("R", C.c_int),
                 ("fc", C.c_double), ("taper", C.c_int), ("spectra_prec", C.c_int),
                 ("phase_weight", C.c_int), ("ck", C.c_double), ("max_frames", C.c_int),
-                ("acc_mode", C.c_int), ("phase_prec", C.c_int)]
+                ("acc_mode", C.c_int), ("phase_prec", C.c_int), ("phase_iters", C.c_int)]
 
 
 class sm_plan_info(C.Structure):
@@ -39,7 +39,8 @@ class sm_plan_info(C.Structure):
 
 class sm_workspace_layout(C.Structure):
     _fields_ = [(n, C.c_size_t) for n in
-                ("spec", "flux", "mu", "P", "M", "noise", "A", "B", "z", "rec", "seeing", "stf", "bytes")]
+                ("spec", "flux", "mu", "P", "M", "noise", "A", "B", "z", "rec", "seeing", "stf", "refine",
+                 "bytes")]
 
 
 class sm_config(C.Structure):

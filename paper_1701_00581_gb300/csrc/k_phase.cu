@@ -98,7 +98,7 @@ __host__ __device__ inline size_t phase_layout(int hb_rows, int pitch, int mri, 
 
 template <typename T>
 __global__ void __launch_bounds__(PH_THREADS, sizeof(T) == 4 ? 2 : 1)
-k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
+k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, const float* __restrict__ P,
         double2* __restrict__ z) {
     using T2 = typename Cx<T>::T2;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -132,7 +132,11 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
         zo[pitch + K] = ay;
     }
 
-    const bool unit = p.weight == SM_W_UNIT;
+    const bool unit = p.weight == SM_W_UNIT, snr = p.weight == SM_W_SNR;
+    const float* Ps = P + (size_t)sl * hb;         // power spectrum, for the SNR weighting
+    auto pget = [&](int kx, int ky) -> T {          // P(-k) = P(k)
+        return (T)(ky >= 0 ? __ldg(Ps + ky * pitch + kx + K) : __ldg(Ps + (-ky) * pitch - kx + K));
+    };
     const float2* Bs = B + (size_t)sl * p.n_tiles * TILE_PAIRS;
     // Stage the item and point records of ring q (< n_rings) into shared
     // memory: items into itm, points into prc[q & 1].
@@ -210,6 +214,14 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M,
                         } else {
                             tx = ty = (T)0;
                         }
+                    } else if (snr) {                   // |B|^2 over the speckle-noise variance of B
+                        const T den = pget(wx - vx, wy - vy) * pget(vx, vy) * pget(wx, wy);
+                        if (den > (T)0) {
+                            tx /= den;
+                            ty /= den;
+                        } else {
+                            tx = ty = (T)0;
+                        }
                     }
                     t[q] = Cx<T>::make(tx, ty);
                 }
@@ -272,17 +284,17 @@ size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_
                         phase_prec == SM_PHASE_FP64 ? sizeof(double2) : sizeof(float2), &a, &b, &c);
 }
 
-cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M,
+cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M, const float* P,
                          double2* z, cudaStream_t st) {
     const size_t sm = phase_smem_bytes(p.hb_rows, p.box_pitch, p.max_ring_items, p.max_ring_points, p.phase_prec);
     if (p.phase_prec == SM_PHASE_FP64) {
         cudaError_t e = cudaFuncSetAttribute(k_phase<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_phase<double><<<nsub, PH_THREADS, sm, st>>>(p, B, M, z);
+        k_phase<double><<<nsub, PH_THREADS, sm, st>>>(p, B, M, P, z);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_phase<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_phase<float><<<nsub, PH_THREADS, sm, st>>>(p, B, M, z);
+        k_phase<float><<<nsub, PH_THREADS, sm, st>>>(p, B, M, P, z);
     }
     return cudaGetLastError();
 }

@@ -94,6 +94,8 @@ extern "C" int sm_workspace_query(const sm_plan* plan, int F, int nsub_chunk, sm
     lay->rec = o; o += al((size_t)d.n_sub * d.N * d.N * sizeof(float));
     lay->seeing = o; o += al((size_t)(d.n_cubes + 1) * sizeof(double));
     lay->stf = o; o += al((size_t)d.N * d.N * sizeof(double));
+    lay->refine = o;
+    if (d.phase_iters > 0) o += al(n * d.n_tiles * (size_t)REF_SLOTS * sizeof(float2));
     lay->bytes = o;
     return SM_OK;
 }
@@ -178,9 +180,13 @@ extern "C" int sm_stage_phase(const sm_plan* plan, int nsub, void* ws, const sm_
     if (rc) return rc;
     if (nsub < 1 || nsub > plan->dev.n_sub) { set_error("bad nsub"); return SM_EINVAL; }
     DeviceGuard g(plan->device);
-    return ret(smk::launch_phase(plan->dev, nsub, at<float2>(ws, lay->B), at<float2>(ws, lay->M),
-                                 at<double2>(ws, lay->z), (cudaStream_t)stream),
-               "phase kernel");
+    rc = ret(smk::launch_phase(plan->dev, nsub, at<float2>(ws, lay->B), at<float2>(ws, lay->M),
+                               at<float>(ws, lay->P), at<double2>(ws, lay->z), (cudaStream_t)stream),
+             "phase kernel");
+    if (rc || plan->dev.phase_iters == 0) return rc;
+    return ret(smk::launch_refine(plan->dev, nsub, at<float2>(ws, lay->B), at<float>(ws, lay->P),
+                                  at<double2>(ws, lay->z), at<float2>(ws, lay->refine), (cudaStream_t)stream),
+               "least-squares phase sweeps");
 }
 
 extern "C" int sm_stage_inverse(const sm_plan* plan, int F, int sub0, int nsub, void* ws,

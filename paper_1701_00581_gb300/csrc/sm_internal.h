@@ -23,6 +23,12 @@ constexpr int TILE_PAIRS = TILE_W * TILE_V;  // 4096 (w, v) slots
 constexpr int BISPEC_THREADS = 32 * VBY;     // one warp per offset row
 static_assert(TILE_V == 32, "a tile row of offsets maps onto the 32 lanes of a warp");
 
+// Least-squares refinement partials per bispectrum tile: one per target w
+// (128), per difference u = w - v of the tile's 11 x 23 rectangle (253) and
+// per offset v (32).
+constexpr int REF_W = TILE_W, REF_U = (WBY + VBY - 1) * (WBX + VBX - 1), REF_V = TILE_V;
+constexpr int REF_SLOTS = REF_W + REF_U + REF_V;   // 413
+
 constexpr float FP16_SCALE = 16384.0f;       // |I_n| <= 1 -> fits half with margin
 constexpr float FP16_INV_SCALE = 1.0f / 16384.0f;
 
@@ -39,6 +45,9 @@ struct PlanDev {
                              //   so that every difference rectangle starts at an even box column
     int prec, weight;
     int acc_mode, phase_prec;
+    int phase_iters;         // least-squares sweeps after the recursion
+    const int* ref_start;    // [n_points + 1] CSR: refinement partial slots of each point
+    const int* ref_idx;      //   tile * REF_SLOTS + slot, bit 31 = conjugate (lower-half occurrence)
     const int4* subs;        // [n_sub] x0, y0, w, h
     const float* winx;       // [n_sub][N] window along x (0 beyond the extent)
     const float* winy;       // [n_sub][N]
@@ -87,7 +96,9 @@ cudaError_t launch_seeing_stf(const smi::PlanDev& p, double* seeing, double* stf
 int seeing_max_bins();   // annuli the seeing kernel holds in shared memory
 cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, int nsub,
                               float2* B, cudaStream_t st);
-cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M,
+cudaError_t launch_refine(const smi::PlanDev& p, int nsub, const float2* B, const float* P, double2* z,
+                          float2* partials, cudaStream_t st);
+cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M, const float* P,
                          double2* z, cudaStream_t st);
 cudaError_t launch_inverse(const smi::PlanDev& p, int F, int sub0, int nsub, const float* A,
                            const double2* z, const float* flux, const float* mu, float* rec,

@@ -64,13 +64,14 @@ int validate_channel(const sm_channel* ch) {
     if (ch->spectra_prec < SM_FP32 || ch->spectra_prec > SM_BF16) {
         set_error("spectra_prec must be SM_FP32, SM_FP16 or SM_BF16"); return SM_EINVAL;
     }
-    if (ch->phase_weight != SM_W_BISPEC && ch->phase_weight != SM_W_UNIT) {
-        set_error("phase_weight must be SM_W_BISPEC or SM_W_UNIT"); return SM_EINVAL;
+    if (ch->phase_weight != SM_W_BISPEC && ch->phase_weight != SM_W_UNIT && ch->phase_weight != SM_W_SNR) {
+        set_error("phase_weight must be SM_W_BISPEC, SM_W_UNIT or SM_W_SNR"); return SM_EINVAL;
     }
     if (ch->max_frames < 1) { set_error("max_frames must be >= 1"); return SM_EINVAL; }
     if (ch->acc_mode != SM_ACC_PLAIN && ch->acc_mode != SM_ACC_KAHAN) {
         set_error("acc_mode must be SM_ACC_PLAIN or SM_ACC_KAHAN"); return SM_EINVAL;
     }
+    if (ch->phase_iters < 0 || ch->phase_iters > 64) { set_error("phase_iters must be in 0..64"); return SM_EINVAL; }
     if (ch->phase_prec != SM_PHASE_FP32 && ch->phase_prec != SM_PHASE_FP64) {
         set_error("phase_prec must be SM_PHASE_FP32 or SM_PHASE_FP64"); return SM_EINVAL;
     }
@@ -114,6 +115,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.r2i = r2i;
     d.prec = ch->spectra_prec; d.weight = ch->phase_weight;
     d.acc_mode = ch->acc_mode; d.phase_prec = ch->phase_prec;
+    d.phase_iters = ch->phase_iters;
     d.box_rows = K + R + 1;
     d.box_cols = 2 * K + 1;
     d.box_pitch = (d.box_cols + 3) / 4 * 4;
@@ -328,6 +330,55 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         return SM_EINVAL;
     }
 
+    // least-squares refinement: for every recursion point, the partial-sum
+    // slots of the refinement's tile pass that hold one of its occurrences
+    // (as w, as u = w - v or as v; lower-half occurrences conjugated), in
+    // tile and slot order, so the gather sums them in a fixed order
+    pl->ref_start.assign(d.n_points + 1, 0);
+    if (ch->phase_iters > 0) {
+        std::vector<int> pt_of((size_t)d.hb_rows * d.box_pitch, -1);
+        for (int pi = 0; pi < d.n_points; ++pi) pt_of[(size_t)pts[pi].y * d.box_pitch + pts[pi].x + K] = pi;
+        std::vector<std::vector<int>> lists(d.n_points);
+        std::vector<char> hit(REF_SLOTS);
+        auto add = [&](int t, int slot, int kx, int ky) {
+            bool conj = false;
+            if (!(ky > 0 || (ky == 0 && kx > 0))) { kx = -kx; ky = -ky; conj = true; }
+            if (ky > K || kx < -K || kx > K) return;
+            const int pi = pt_of[(size_t)ky * d.box_pitch + kx + K];
+            if (pi < 0) return;                                     // anchor or outside the domain
+            lists[pi].push_back((t * REF_SLOTS + slot) | (conj ? (int)0x80000000u : 0));
+        };
+        for (int t = 0; t < d.n_tiles; ++t) {
+            const int4 T = pl->tiles[t];
+            std::fill(hit.begin(), hit.end(), 0);
+            for (int row = 0; row < WBY; ++row)
+                for (int col = 0; col < WBX; ++col)
+                    for (int q = 0; q < VBY; ++q)
+                        for (int kk = 0; kk < VBX; ++kk) {
+                            if (!pair_used_host(T.x + col, T.y + row, T.z + kk, T.w + q, r2i, R * R)) continue;
+                            hit[row * WBX + col] = 1;
+                            hit[REF_W + (row - q + VBY - 1) * (WBX + VBX - 1) + col - kk + VBX - 1] = 1;
+                            hit[REF_W + REF_U + q * VBX + kk] = 1;
+                        }
+            for (int sl = 0; sl < REF_SLOTS; ++sl) {
+                if (!hit[sl]) continue;
+                if (sl < REF_W) {
+                    add(t, sl, T.x + sl % WBX, T.y + sl / WBX);
+                } else if (sl < REF_W + REF_U) {
+                    const int c = sl - REF_W, ur = c / (WBX + VBX - 1), uc = c % (WBX + VBX - 1);
+                    add(t, sl, T.x - T.z - (VBX - 1) + uc, T.y - T.w - (VBY - 1) + ur);
+                } else {
+                    const int c = sl - REF_W - REF_U;
+                    add(t, sl, T.z + c % VBX, T.w + c / VBX);
+                }
+            }
+        }
+        for (int pi = 0; pi < d.n_points; ++pi) {
+            pl->ref_start[pi + 1] = pl->ref_start[pi] + (int)lists[pi].size();
+            pl->ref_idx.insert(pl->ref_idx.end(), lists[pi].begin(), lists[pi].end());
+        }
+    }
+
     // upload all tables in one allocation
     struct Piece { const void* src; size_t bytes; size_t off; };
     std::vector<Piece> pcs = {
@@ -350,6 +401,8 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         {pl->cube_of_sub.data(), pl->cube_of_sub.size() * sizeof(int), 0},
         {pl->ann_start.data(), pl->ann_start.size() * sizeof(int), 0},
         {pl->ann_idx.data(), pl->ann_idx.size() * sizeof(int), 0},
+        {pl->ref_start.data(), pl->ref_start.size() * sizeof(int), 0},
+        {pl->ref_idx.data(), pl->ref_idx.size() * sizeof(int), 0},
     };
     size_t total = 0;
     for (auto& p : pcs) { p.off = total; total += align256(std::max<size_t>(p.bytes, 1)); }
@@ -382,6 +435,8 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.cube_of_sub = (const int*)at(16);
     d.ann_start = (const int*)at(17);
     d.ann_idx = (const int*)at(18);
+    d.ref_start = (const int*)at(19);
+    d.ref_idx = (const int*)at(20);
     *out = pl;
     return SM_OK;
 }

@@ -22,6 +22,7 @@ struct sm_plan {
     std::vector<int4> point_rec;
     std::vector<int> cubes, cube_of_sub;   // seeing cubes (subfield ids), subfield -> cube or -1
     std::vector<int> ann_start, ann_idx;   // annuli of the half-plane domain
+    std::vector<int> ref_start, ref_idx;   // refinement partial slots of each recursion point
     long long n_pairs = 0;
     int n_U = 0, n_V = 0;
     void* dmem = nullptr;            // device copy of every table

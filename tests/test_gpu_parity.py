@@ -226,23 +226,33 @@ def test_invalid_stage_arguments_fail_cleanly(ragged):
 
 
 @pytest.mark.parametrize("name,kw", [("unit_weights", dict(phase_weight=1)),
+                                     ("snr_weights", dict(phase_weight=2)),
+                                     ("least_squares_5", dict(phase_iters=5)),
+                                     ("least_squares_snr_3", dict(phase_weight=2, phase_iters=3)),
                                      ("overlap75", dict(stride=16)),
                                      ("chain_R1", dict(R=1))])
 def test_method_variants_match_oracle(torch, name, kw):
-    """Unit-modulus phase terms, a 75 % overlap grid (stride N/4, as in the
-    paper's own 1110-cube layout) and R = 1 (single-path recursion), each
-    against the oracle run with the same parameters."""
+    """Unit-modulus and SNR-weighted phase terms, least-squares sweeps after
+    the recursion, a 75 % overlap grid (stride N/4, as in the paper's own
+    1110-cube layout) and R = 1 (single-path recursion), each against the
+    oracle run with the same parameters."""
     from paper_1701_00581_gb300 import Channel, Plan
     c = CS.case("ragged")
     sp = c["spec"]
     stride = kw.get("stride", c["stride"])
     R = kw.get("R", c["R"])
     weight = kw.get("phase_weight", O.W_BISPEC)
+    iters = kw.get("phase_iters", 0)
     plan = Plan(Channel(W=sp.W, H=sp.H, N=c["N"], R=R, stride=stride, fc=CS.FC, taper=c["taper"],
-                        phase_weight=weight, max_frames=sp.F))
+                        phase_weight=weight, phase_iters=iters, max_frames=sp.F))
     b = CS.burst("ragged")
     g = CS.gpu_run(plan, b["frames"], b["stf_emp"])
-    o = O.reconstruct_burst(b["frames"], c["N"], stride, CS.FC, R, c["taper"], b["stf_emp"], weight)
+    o = O.reconstruct_burst(b["frames"], c["N"], stride, CS.FC, R, c["taper"], b["stf_emp"], weight,
+                            iters=iters)
+    if iters:
+        # the sweeps sum in a fixed order: a second run is bitwise equal
+        g2 = CS.gpu_run(plan, b["frames"], b["stf_emp"])
+        assert np.array_equal(g2["z"], g["z"]) and np.array_equal(g2["out"], g["out"])
     assert plan.info["n_sub"] == len(o["subs"])
     wv = CS.used_pairs(c["N"], R)
     idx = plan.pair_index(wv)
