@@ -17,9 +17,12 @@
 // per difference over the tile's splits in shared memory, per offset along
 // a warp shuffle tree.  The tile touches 413 distinct frequencies (its
 // targets, offsets and differences); their phasors (and powers, for the SNR
-// weighting) are staged in shared memory first.  k_refine_gather: one CTA per subfield, one warp per recursion
-// point, sums the point's partials from the plan's list along a fixed tree
-// and renormalises.  No atomics: the result does not depend on scheduling.
+// weighting) are staged in shared memory first, and each thread issues the
+// loads of its 32 stored values before using any.
+//
+// k_refine_gather: eight CTAs per subfield, one warp per recursion point,
+// sums the point's partials from the plan's list along a fixed tree and
+// renormalises.  No atomics: the result does not depend on scheduling.
 #include "sm_internal.h"
 
 namespace {
@@ -35,6 +38,7 @@ using smi::TILE_V;
 constexpr int RT_THREADS = smi::BISPEC_THREADS;     // 128: 4 warps = 4 offset rows
 constexpr int UCOLS = smi::WBX + smi::VBX - 1;      // 23 difference columns
 constexpr int RG_THREADS = 512;
+constexpr int RG_BLOCKS = 8;                        // gather CTAs per subfield
 
 __device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2i, int R2) {
     const int w2 = wx * wx + wy * wy, v2 = vx * vx + vy * vy;
@@ -104,13 +108,21 @@ k_refine_tiles(PlanDev p, const float2* __restrict__ B, const float* __restrict_
         float2 sw = make_float2(0.f, 0.f);
         const float2 zw = zt[wslot];
         const float pw = pt[wslot];
+        // the 8 stored values of this target's offset row are 64 contiguous
+        // bytes: four independent 16-byte loads, issued before any use (a
+        // slot of an unused pair may hold anything; it is never used)
+        const float4* b4 = reinterpret_cast<const float4*>(Bt + wslot * TILE_V + q * smi::VBX);
+        float4 bq[smi::VBX / 2];
+#pragma unroll
+        for (int h = 0; h < smi::VBX / 2; ++h) bq[h] = __ldg(b4 + h);
 #pragma unroll
         for (int kk = 0; kk < smi::VBX; ++kk) {
             const int vx = vx0 + kk;
             const int slot = wslot * TILE_V + q * smi::VBX + kk;
             float2 tu = make_float2(0.f, 0.f);
             if (pair_used(wx, wy, vx, vy, p.r2i, R2)) {
-                const float2 b = Bt[slot];
+                const float2 b = (kk & 1) ? make_float2(bq[kk >> 1].z, bq[kk >> 1].w)
+                                          : make_float2(bq[kk >> 1].x, bq[kk >> 1].y);
                 const int ucell = REF_W + (wyl - q + smi::VBY - 1) * UCOLS + 4 * gx + j - kk + smi::VBX - 1;
                 const int vcell = REF_W + REF_U + q * smi::VBX + kk;
                 const float2 zu = zt[ucell];
@@ -182,17 +194,24 @@ k_refine_tiles(PlanDev p, const float2* __restrict__ B, const float* __restrict_
 
 __global__ void __launch_bounds__(RG_THREADS)
 k_refine_gather(PlanDev p, const float2* __restrict__ partials, double2* __restrict__ z) {
-    const int sl = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sl = blockIdx.x, lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.y * (RG_THREADS / 32) + (threadIdx.x >> 5);
+    const int nwarp = gridDim.y * (RG_THREADS / 32);
     const int K = p.K, pitch = p.box_pitch;
     double2* zs = z + (size_t)sl * p.hb_rows * pitch;
     const float2* part = partials + (size_t)sl * p.n_tiles * REF_SLOTS;
-    for (int pi = warp; pi < p.n_points; pi += RG_THREADS / 32) {
+    for (int pi = gwarp; pi < p.n_points; pi += nwarp) {
         double sx = 0.0, sy = 0.0;
-        for (int a = p.ref_start[pi] + lane; a < p.ref_start[pi + 1]; a += 32) {
-            const int e = p.ref_idx[a];
-            const float2 c = part[e & 0x7fffffff];
-            sx += c.x;
-            sy += e < 0 ? -(double)c.y : (double)c.y;
+        const int a0 = p.ref_start[pi], a1 = p.ref_start[pi + 1];
+        // two entries per lane per step, both loads in flight together
+        for (int a = a0 + lane; a < a1; a += 64) {
+            const bool two = a + 32 < a1;
+            const int e0 = p.ref_idx[a];
+            const int e1 = two ? p.ref_idx[a + 32] : 0;
+            const float2 c0 = part[e0 & 0x7fffffff];
+            const float2 c1 = two ? part[e1 & 0x7fffffff] : make_float2(0.f, 0.f);
+            sx += (double)c0.x + (double)c1.x;
+            sy += (e0 < 0 ? -(double)c0.y : (double)c0.y) + (e1 < 0 ? -(double)c1.y : (double)c1.y);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -219,7 +238,7 @@ cudaError_t launch_refine(const smi::PlanDev& p, int nsub, const float2* B, cons
                           float2* partials, cudaStream_t st) {
     for (int it = 0; it < p.phase_iters; ++it) {
         k_refine_tiles<<<dim3(p.n_tiles, nsub), RT_THREADS, 0, st>>>(p, B, P, z, partials);
-        k_refine_gather<<<nsub, RG_THREADS, 0, st>>>(p, partials, z);
+        k_refine_gather<<<dim3(nsub, RG_BLOCKS), RG_THREADS, 0, st>>>(p, partials, z);
     }
     return cudaGetLastError();
 }
