@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--phase", default="fp32", choices=["fp32", "fp64"], help="recursion arithmetic")
     ap.add_argument("--weight", default="bispec", choices=["bispec", "unit", "snr"], help="phase-term weighting")
     ap.add_argument("--iters", type=int, default=0, help="least-squares phase sweeps after the recursion")
+    ap.add_argument("--inflight", type=int, default=2, help="bursts in flight on the served e2e path")
     ap.add_argument("--size", default=None,
                     help="WxH override (profiling a smaller case of the same kernels)")
     return ap.parse_args()
@@ -422,9 +423,10 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         host_frames = torch.from_numpy(b["frames"]).pin_memory()
-        host_out = [torch.empty((spec.H, spec.W), dtype=torch.float32).pin_memory() for _ in range(2)]
-        host_valid = [torch.empty((spec.H, spec.W), dtype=torch.uint8).pin_memory() for _ in range(2)]
-        eng = Engine([ch], hbm_budget_bytes=int(100e9), max_inflight=2, device=local)
+        K_IN = max(1, args.inflight)
+        host_out = [torch.empty((spec.H, spec.W), dtype=torch.float32).pin_memory() for _ in range(K_IN)]
+        host_valid = [torch.empty((spec.H, spec.W), dtype=torch.uint8).pin_memory() for _ in range(K_IN)]
+        eng = Engine([ch], hbm_budget_bytes=int(120e9), max_inflight=K_IN, device=local)
         fr_np = host_frames.numpy()
 
         def serve(n):
@@ -432,8 +434,8 @@ def main():
             submitted = done = 0
             t_start = time.perf_counter()
             while done < n:
-                while submitted < n and len(pending) < 2:
-                    k = submitted % 2
+                while submitted < n and len(pending) < K_IN:
+                    k = submitted % K_IN
                     tk = eng.try_submit(0, fr_np, host_out[k].numpy(), host_valid[k].numpy())
                     if tk is None:
                         break
@@ -456,7 +458,7 @@ def main():
                "d2h_bytes_per_step": int(spec.W * spec.H * 5),
                "latency_ms_p50": 1000 * float(np.percentile(lat, 50)),
                "latency_ms_p99": 1000 * float(np.percentile(lat, 99)),
-               "max_inflight": 2}
+               "max_inflight": K_IN, "hbm_budget_gb": 120}
 
     serving = None
     if not args.no_serve and args.workload == "tio2560" and not args.size:
