@@ -38,6 +38,10 @@ using smi::TILE_V;
 constexpr int RT_THREADS = smi::BISPEC_THREADS;     // 128: 4 warps = 4 offset rows
 constexpr int UCOLS = smi::WBX + smi::VBX - 1;      // 23 difference columns
 constexpr int RG_THREADS = 512;
+// contributions to the differences, one row of 32 slots per target padded
+// to 33: lanes of a warp hold different targets, so an unpadded row pitch
+// of 32 float2 put all 32 lanes on one shared-memory bank
+constexpr int CU_PITCH = TILE_V + 1;
 constexpr int RG_BLOCKS = 8;                        // gather CTAs per subfield
 
 __device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2i, int R2) {
@@ -70,7 +74,7 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 __global__ void __launch_bounds__(RT_THREADS)
 k_refine_tiles(PlanDev p, const float2* __restrict__ B, const float* __restrict__ P,
                const double2* __restrict__ z, float2* __restrict__ partials) {
-    __shared__ float2 cu[TILE_PAIRS];             // contributions to u = w - v, by slot
+    __shared__ float2 cu[smi::TILE_W * CU_PITCH]; // contributions to u = w - v: [target][offset slot]
     __shared__ float2 cw[smi::VBY][REF_W];        // per offset row: contributions to each target
     __shared__ float2 zt[REF_SLOTS];              // phasors of the tile's targets | differences | offsets
     __shared__ float pt[REF_SLOTS];               // their powers (SNR weighting)
@@ -118,7 +122,6 @@ k_refine_tiles(PlanDev p, const float2* __restrict__ B, const float* __restrict_
 #pragma unroll
         for (int kk = 0; kk < smi::VBX; ++kk) {
             const int vx = vx0 + kk;
-            const int slot = wslot * TILE_V + q * smi::VBX + kk;
             float2 tu = make_float2(0.f, 0.f);
             if (pair_used(wx, wy, vx, vy, p.r2i, R2)) {
                 const float2 b = (kk & 1) ? make_float2(bq[kk >> 1].z, bq[kk >> 1].w)
@@ -144,7 +147,7 @@ k_refine_tiles(PlanDev p, const float2* __restrict__ B, const float* __restrict_
                 sv[kk].x += g * c2.x;
                 sv[kk].y += g * c2.y;
             }
-            cu[slot] = tu;
+            cu[wslot * CU_PITCH + q * smi::VBX + kk] = tu;
         }
         cw[q][wslot] = sw;
     }
@@ -171,7 +174,7 @@ k_refine_tiles(PlanDev p, const float2* __restrict__ B, const float* __restrict_
             for (int kk = 0; kk < smi::VBX; ++kk) {
                 const int tc = uc + kk - (smi::VBX - 1);
                 if (tc < 0 || tc >= smi::WBX) continue;
-                const float2 c = cu[(tr * smi::WBX + tc) * TILE_V + qq * smi::VBX + kk];
+                const float2 c = cu[(tr * smi::WBX + tc) * CU_PITCH + qq * smi::VBX + kk];
                 s.x += c.x;
                 s.y += c.y;
             }
