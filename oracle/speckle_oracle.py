@@ -57,14 +57,19 @@ W_SNR = 2        # terms weighted by |B| / (P(u) P(v) P(w)), i.e. |B|^2 over its
 # ----------------------------------------------------------------------------
 # subfields and window (Sect. 2: partially overlapping subimage cubes)
 # ----------------------------------------------------------------------------
-def subfield_grid(W: int, H: int, N: int, stride: int) -> List[Tuple[int, int, int, int]]:
+def subfield_grid(W: int, H: int, N: int, stride: int,
+                  drop_edge: bool = False) -> List[Tuple[int, int, int, int]]:
     """Overlapping subfields (x0, y0, w, h), row-major over y then x.
 
     The paper cuts each frame into partially overlapping cubes matching the
     isoplanatic patch (Sect. 2, Sect. 3.2).  Reading: tiles start every
     ``stride`` px; a ragged last tile keeps its true extent ``w, h < N``.
+    With ``drop_edge`` only full N x N tiles are kept: at stride 64 this is
+    the paper's own 37 x 30 = 1110 cubes of a 2560 x 2160 burst (Sect. 3.2).
     """
     def starts(L: int) -> List[int]:
+        if drop_edge:
+            return [k * stride for k in range((L - N) // stride + 1)] if L >= N else []
         n = 1 if L <= N else int(math.ceil((L - N) / stride)) + 1
         return [k * stride for k in range(n)]
 
@@ -671,6 +676,34 @@ def mosaic(recs: Sequence[np.ndarray], subs: Sequence[Tuple[int, int, int, int]]
     return out, valid
 
 
+def mosaic_central(recs: Sequence[np.ndarray], subs: Sequence[Tuple[int, int, int, int]], W: int,
+                   H: int, N: int, stride: int, taper: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Merge full-size sub-images by their central stride x stride blocks.
+
+    The paper merges the aligned sub-images into a 2368 x 1920 mosaic from
+    1110 cubes of 256^2 at stride 64 (Sect. 3.2): 37 x 30 blocks of 64^2,
+    the central block of each sub-image, so every mosaic pixel comes from
+    the one sub-image whose centre is nearest and the partial images sum
+    without overlap.  Block of subfield (x0, y0): [x0 + (N - s)/2,
+    x0 + (N + s)/2) on each axis; the value is rec / window there (the
+    window is 1 inside the block for taper <= (N - s)/2).  Pixels outside
+    every block are invalid and 0.
+    """
+    if (N - stride) % 2:
+        raise ValueError("the central block needs N - stride even")
+    h0 = (N - stride) // 2
+    out = np.zeros((H, W))
+    valid = np.zeros((H, W), dtype=bool)
+    for rec, (x0, y0, w, h) in zip(recs, subs):
+        if w != N or h != N:
+            raise ValueError("the central-block mosaic takes full-size sub-images")
+        win = window2d(N, N, taper)
+        blk = (slice(h0, h0 + stride), slice(h0, h0 + stride))
+        out[y0 + h0:y0 + h0 + stride, x0 + h0:x0 + h0 + stride] = rec[blk] / win[blk]
+        valid[y0 + h0:y0 + h0 + stride, x0 + h0:x0 + h0 + stride] = True
+    return out, valid
+
+
 # ----------------------------------------------------------------------------
 # whole path
 # ----------------------------------------------------------------------------
@@ -698,24 +731,30 @@ def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: 
 def reconstruct_burst(frames: np.ndarray, N: int, stride: int, fc: float, R: int, taper: int,
                       stf: Optional[np.ndarray], weight: int = W_BISPEC,
                       subfields: Optional[Sequence[int]] = None, ck: float = 0.435,
-                      iters: int = 0) -> Dict:
+                      iters: int = 0, paper_layout: bool = False) -> Dict:
     """Whole burst: every subfield (or the listed ones), then the mosaic.
 
     With ``stf`` None the STF is the model at the seeing estimated from the
-    burst itself (Sect. 3.1, ``estimate_seeing``), as the paper does.
+    burst itself (Sect. 3.1, ``estimate_seeing``), as the paper does.  With
+    ``paper_layout`` only full tiles are kept and the mosaic takes their
+    central blocks (``mosaic_central``).
     """
     F, H, W = frames.shape
     seeing = None
     if stf is None:
         seeing = estimate_seeing(frames, N, stride, fc, taper, ck)
         stf = stf_model(N, fc, [seeing[1]], ck)
-    subs = subfield_grid(W, H, N, stride)
+    subs = subfield_grid(W, H, N, stride, drop_edge=paper_layout)
     pairs = pair_domain(N, fc, R)
     pick = range(len(subs)) if subfields is None else subfields
     results = {s: reconstruct_subfield(frames, subs[s], N, fc, R, taper, stf, weight, pairs, iters)
                for s in pick}
     out = valid = None
     if subfields is None:
-        out, valid = mosaic([results[s]["rec"] for s in range(len(subs))], subs, W, H, taper)
+        recs = [results[s]["rec"] for s in range(len(subs))]
+        if paper_layout:
+            out, valid = mosaic_central(recs, subs, W, H, N, stride, taper)
+        else:
+            out, valid = mosaic(recs, subs, W, H, taper)
     return {"subs": subs, "pairs": pairs, "sub": results, "out": out, "valid": valid,
             "seeing": seeing, "stf": stf}

@@ -513,3 +513,40 @@ def test_estimate_seeing_orders_bursts_by_seeing():
     assert est[5.0] < est[12.0]
     for d, x in est.items():
         assert d / 1.5 < x < d * 1.5
+
+
+# ---------------------------------------------------------------------------
+# the paper's layout (Sect. 3.2): 1110 cubes, 2368 x 1920 mosaic
+# ---------------------------------------------------------------------------
+
+def test_paper_layout_matches_the_papers_counts():
+    subs = O.subfield_grid(2560, 2160, 256, 64, drop_edge=True)
+    assert len(subs) == 1110 and all(w == 256 and h == 256 for _, _, w, h in subs)
+    assert subs[-1] == (2304, 1856, 256, 256)
+    recs = [np.ones((256, 256)) for _ in subs]
+    out, valid = O.mosaic_central(recs, subs, 2560, 2160, 256, 64, 32)
+    ys, xs = np.nonzero(valid)
+    assert (ys.min(), ys.max() + 1, xs.min(), xs.max() + 1) == (96, 2016, 96, 2464)
+    assert valid.sum() == 2368 * 1920
+    assert np.all(out[valid] == 1.0)
+
+
+def test_mosaic_central_is_a_partition_by_nearest_centre():
+    W, H, N, s, taper = 200, 150, 32, 8, 4
+    subs = O.subfield_grid(W, H, N, s, drop_edge=True)
+    win = O.window2d(N, N, taper)
+    recs = []
+    for i in range(len(subs)):
+        y, x = np.mgrid[0:N, 0:N]
+        recs.append((i * 10000 + y * 100 + x) * win)       # rec carries the window
+    out, valid = O.mosaic_central(recs, subs, W, H, N, s, taper)
+    for py in range(H):
+        for px in range(W):
+            owners = [i for i, (x0, y0, w, h) in enumerate(subs)
+                      if x0 + (N - s) // 2 <= px < x0 + (N + s) // 2 and y0 + (N - s) // 2 <= py < y0 + (N + s) // 2]
+            assert len(owners) <= 1
+            assert valid[py, px] == (len(owners) == 1)
+            if owners:
+                i = owners[0]
+                x0, y0 = subs[i][:2]
+                assert out[py, px] == pytest.approx(i * 10000 + (py - y0) * 100 + (px - x0), rel=1e-12)
