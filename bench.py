@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--weight", default="bispec", choices=["bispec", "unit", "snr"], help="phase-term weighting")
     ap.add_argument("--iters", type=int, default=0, help="least-squares phase sweeps after the recursion")
     ap.add_argument("--inflight", type=int, default=2, help="bursts in flight on the served e2e path")
+    ap.add_argument("--layout", default="overlap50", choices=["overlap50", "paper"],
+                    help="overlap50: stride N/2, ragged edges padded, blended mosaic; paper: stride N/4, "
+                         "full tiles only, central-block mosaic (1110 cubes, 2368x1920 for TiO)")
     ap.add_argument("--size", default=None,
                     help="WxH override (profiling a smaller case of the same kernels)")
     return ap.parse_args()
@@ -310,12 +313,15 @@ def main():
     b = make_burst(spec, channel=1, burst=rank, device=f"cuda:{local}")
     F = spec.F
     from paper_1701_00581_gb300 import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_FP16, SM_FP32,
-                                        SM_PHASE_FP32, SM_PHASE_FP64, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT)
+                                        SM_PHASE_FP32, SM_PHASE_FP64, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT,
+                                        SM_EDGE_DROP, SM_MOSAIC_CENTRAL)
     modes = dict(spectra_prec={"fp32": SM_FP32, "fp16": SM_FP16, "bf16": SM_BF16}[args.spectra],
                  acc_mode={"plain": SM_ACC_PLAIN, "kahan": SM_ACC_KAHAN}[args.acc],
                  phase_prec={"fp32": SM_PHASE_FP32, "fp64": SM_PHASE_FP64}[args.phase],
                  phase_weight={"bispec": SM_W_BISPEC, "unit": SM_W_UNIT, "snr": SM_W_SNR}[args.weight],
                  phase_iters=args.iters)
+    if args.layout == "paper":
+        modes.update(stride=N // 4, edge_mode=SM_EDGE_DROP, mosaic_mode=SM_MOSAIC_CENTRAL)
     ch = Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=F, **modes)
     plan = Plan(ch, device=local)
     info = plan.info
@@ -479,7 +485,10 @@ def main():
                 "dtype": "f32" if args.spectra == "fp32" else f"{args.spectra} spectra, f32 arithmetic",
                 "data": "synthetic",
                 "config": {"workload": f"{args.workload} burst: {spec.W}x{spec.H}x{F} uint16, "
-                                       f"{n_sub} subfields of {N}^2 at 50% overlap, |v|<={R}",
+                                       f"{n_sub} subfields of {N}^2 at "
+                                       + ("50% overlap" if args.layout == "overlap50" else
+                                          "75% overlap, full tiles, central-block mosaic (the paper's layout)")
+                                       + f", |v|<={R}",
                            "path": "plain per-burst stages",
                            "precision": f"spectra {args.spectra}, bispectrum sums {args.acc} fp32, "
                                         f"recursion {args.phase}",

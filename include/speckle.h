@@ -66,6 +66,15 @@ extern "C" {
                            * subfield streams its frames twice (half of the
                            * offsets per pass), about 2.5x the time          */
 
+#define SM_EDGE_PAD  0     /* ragged last subfields kept, zero-padded to N     */
+#define SM_EDGE_DROP 1     /* full N x N subfields only (the paper's layout)   */
+
+#define SM_MOSAIC_BLEND   0 /* out = sum rec / sum window, valid where >= 0.25 */
+#define SM_MOSAIC_CENTRAL 1 /* each pixel from the central stride x stride block
+                             * of one sub-image (the paper's 2368 x 1920 mosaic
+                             * from 1110 cubes at stride 64); needs
+                             * SM_EDGE_DROP and N - stride even               */
+
 #define SM_PHASE_FP32 0   /* phase recursion arithmetic FP32, phasors stored FP64 */
 #define SM_PHASE_FP64 1   /* phase recursion arithmetic FP64 throughout       */
 
@@ -85,6 +94,8 @@ typedef struct {
     int    phase_prec;    /* SM_PHASE_FP32 / SM_PHASE_FP64                     */
     int    phase_iters;   /* least-squares sweeps after the recursion (0..64);
                            * see sm_stage_phase                               */
+    int    edge_mode;     /* SM_EDGE_PAD / SM_EDGE_DROP                        */
+    int    mosaic_mode;   /* SM_MOSAIC_BLEND / SM_MOSAIC_CENTRAL               */
 } sm_channel;
 
 /* ======================================================================== *
@@ -227,8 +238,11 @@ int sm_stage_inverse(const sm_plan* plan, int F, int sub0, int nsub, void* ws,
                      const sm_workspace_layout* lay, void* stream);
 
 /* Sect. 3.2 merge: out = sum_s rec_s / sum_s window_s over all subfields;
- * valid = (sum window >= 0.25), out = 0 elsewhere.  out: device float
- * [H][W]; valid: device uint8 [H][W] or NULL.                               */
+ * valid = (sum window >= 0.25), out = 0 elsewhere.  With SM_MOSAIC_CENTRAL
+ * each pixel inside the central stride x stride block of a subfield
+ * [x0 + (N-s)/2, x0 + (N+s)/2)^2 is rec / window of that subfield, valid;
+ * every other pixel 0, invalid.  out: device float [H][W]; valid: device
+ * uint8 [H][W] or NULL.                                                     */
 int sm_stage_mosaic(const sm_plan* plan, void* ws, const sm_workspace_layout* lay,
                     float* out, uint8_t* valid, void* stream);
 

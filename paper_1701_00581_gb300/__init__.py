@@ -13,7 +13,8 @@ from typing import Dict, Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_F32, SM_FP16, SM_FP32,  # noqa: F401
+from ._lib import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_EDGE_DROP, SM_EDGE_PAD, SM_F32,  # noqa: F401
+                   SM_FP16, SM_FP32, SM_MOSAIC_BLEND, SM_MOSAIC_CENTRAL,
                    SM_PHASE_FP32, SM_PHASE_FP64, SM_U16, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT, SpeckleError,
                    check, load)
 
@@ -37,12 +38,15 @@ class Channel:
     acc_mode: int = SM_ACC_PLAIN
     phase_prec: int = SM_PHASE_FP32
     phase_iters: int = 0
+    edge_mode: int = SM_EDGE_PAD
+    mosaic_mode: int = SM_MOSAIC_BLEND
 
     def to_c(self) -> _lib.sm_channel:
         return _lib.sm_channel(
             self.W, self.H, self.N, self.stride if self.stride is not None else self.N // 2, self.R,
             self.fc, self.taper if self.taper is not None else self.N // 8, self.spectra_prec,
-            self.phase_weight, self.ck, self.max_frames, self.acc_mode, self.phase_prec, self.phase_iters)
+            self.phase_weight, self.ck, self.max_frames, self.acc_mode, self.phase_prec, self.phase_iters,
+            self.edge_mode, self.mosaic_mode)
 
 
 def _ptr(t) -> Optional[int]:

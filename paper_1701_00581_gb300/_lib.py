@@ -20,13 +20,16 @@ SM_W_BISPEC, SM_W_UNIT, SM_W_SNR = 0, 1, 2
 SM_U16, SM_F32 = 0, 1
 SM_ACC_PLAIN, SM_ACC_KAHAN = 0, 1
 SM_PHASE_FP32, SM_PHASE_FP64 = 0, 1
+SM_EDGE_PAD, SM_EDGE_DROP = 0, 1
+SM_MOSAIC_BLEND, SM_MOSAIC_CENTRAL = 0, 1
 
 
 class sm_channel(C.Structure):
     _fields_ = [("W", C.c_int), ("H", C.c_int), ("N", C.c_int), ("stride", C.c_int), ("R", C.c_int),
                 ("fc", C.c_double), ("taper", C.c_int), ("spectra_prec", C.c_int),
                 ("phase_weight", C.c_int), ("ck", C.c_double), ("max_frames", C.c_int),
-                ("acc_mode", C.c_int), ("phase_prec", C.c_int), ("phase_iters", C.c_int)]
+                ("acc_mode", C.c_int), ("phase_prec", C.c_int), ("phase_iters", C.c_int),
+                ("edge_mode", C.c_int), ("mosaic_mode", C.c_int)]
 
 
 class sm_plan_info(C.Structure):

@@ -108,6 +108,23 @@ __global__ void k_mosaic(PlanDev p, const float* __restrict__ rec, float* __rest
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= p.W || y >= p.H) return;
+    if (p.mosaic_mode == SM_MOSAIC_CENTRAL) {
+        // the one subfield whose central stride x stride block holds (x, y)
+        const int h0 = (p.N - p.stride) / 2;
+        const int i = x >= h0 ? (x - h0) / p.stride : -1, j = y >= h0 ? (y - h0) / p.stride : -1;
+        const bool ok = i >= 0 && i < p.nsx && j >= 0 && j < p.nsy;
+        float v = 0.f;
+        if (ok) {
+            const int s = j * p.nsx + i;
+            const int4 sb = p.subs[s];
+            const int lx = x - sb.x, ly = y - sb.y;       // in [h0, h0 + stride)
+            v = rec[((size_t)s * p.N + ly) * p.N + lx] /
+                (p.winx[(size_t)s * p.N + lx] * p.winy[(size_t)s * p.N + ly]);
+        }
+        out[(size_t)y * p.W + x] = v;
+        if (valid) valid[(size_t)y * p.W + x] = ok ? 1 : 0;
+        return;
+    }
     const int ilo = x - p.N + 1 > 0 ? (x - p.N + p.stride) / p.stride : 0;
     const int ihi = min(p.nsx - 1, x / p.stride);
     const int jlo = y - p.N + 1 > 0 ? (y - p.N + p.stride) / p.stride : 0;

@@ -46,6 +46,7 @@ struct PlanDev {
     int prec, weight;
     int acc_mode, phase_prec;
     int phase_iters;         // least-squares sweeps after the recursion
+    int mosaic_mode;         // SM_MOSAIC_BLEND / SM_MOSAIC_CENTRAL
     const int* ref_start;    // [n_points + 1] CSR: refinement partial slots of each point
     const int* ref_idx;      //   tile * REF_SLOTS + slot, bit 31 = conjugate (lower-half occurrence)
     const int4* subs;        // [n_sub] x0, y0, w, h

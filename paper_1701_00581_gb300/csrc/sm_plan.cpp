@@ -21,9 +21,10 @@ int cuda_fail(cudaError_t e, const char* where) {
 }
 
 // Sect. 2: partially overlapping subfields; ragged edge tiles keep their
-// true extent.
-static std::vector<int> tile_starts(int L, int N, int stride) {
-    int n = L <= N ? 1 : (int)std::ceil((double)(L - N) / stride) + 1;
+// true extent, or (drop) only full tiles are kept, as in the paper's 1110
+// cubes (Sect. 3.2).
+static std::vector<int> tile_starts(int L, int N, int stride, bool drop) {
+    int n = drop ? (L - N) / stride + 1 : (L <= N ? 1 : (int)std::ceil((double)(L - N) / stride) + 1);
     std::vector<int> s(n);
     for (int k = 0; k < n; ++k) s[k] = k * stride;
     return s;
@@ -72,6 +73,18 @@ int validate_channel(const sm_channel* ch) {
         set_error("acc_mode must be SM_ACC_PLAIN or SM_ACC_KAHAN"); return SM_EINVAL;
     }
     if (ch->phase_iters < 0 || ch->phase_iters > 64) { set_error("phase_iters must be in 0..64"); return SM_EINVAL; }
+    if (ch->edge_mode != SM_EDGE_PAD && ch->edge_mode != SM_EDGE_DROP) {
+        set_error("edge_mode must be SM_EDGE_PAD or SM_EDGE_DROP"); return SM_EINVAL;
+    }
+    if (ch->edge_mode == SM_EDGE_DROP && (ch->W < ch->N || ch->H < ch->N)) {
+        set_error("SM_EDGE_DROP needs a frame of at least N x N"); return SM_EINVAL;
+    }
+    if (ch->mosaic_mode != SM_MOSAIC_BLEND && ch->mosaic_mode != SM_MOSAIC_CENTRAL) {
+        set_error("mosaic_mode must be SM_MOSAIC_BLEND or SM_MOSAIC_CENTRAL"); return SM_EINVAL;
+    }
+    if (ch->mosaic_mode == SM_MOSAIC_CENTRAL && (ch->edge_mode != SM_EDGE_DROP || (ch->N - ch->stride) % 2)) {
+        set_error("SM_MOSAIC_CENTRAL needs SM_EDGE_DROP and N - stride even"); return SM_EINVAL;
+    }
     if (ch->phase_prec != SM_PHASE_FP32 && ch->phase_prec != SM_PHASE_FP64) {
         set_error("phase_prec must be SM_PHASE_FP32 or SM_PHASE_FP64"); return SM_EINVAL;
     }
@@ -116,13 +129,15 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.prec = ch->spectra_prec; d.weight = ch->phase_weight;
     d.acc_mode = ch->acc_mode; d.phase_prec = ch->phase_prec;
     d.phase_iters = ch->phase_iters;
+    d.mosaic_mode = ch->mosaic_mode;
     d.box_rows = K + R + 1;
     d.box_cols = 2 * K + 1;
     d.box_pitch = (d.box_cols + 3) / 4 * 4;
     d.hb_rows = K + 1;
 
     // subfield grid
-    auto xs = tile_starts(ch->W, N, ch->stride), ys = tile_starts(ch->H, N, ch->stride);
+    const bool drop = ch->edge_mode == SM_EDGE_DROP;
+    auto xs = tile_starts(ch->W, N, ch->stride, drop), ys = tile_starts(ch->H, N, ch->stride, drop);
     d.nsx = (int)xs.size(); d.nsy = (int)ys.size(); d.n_sub = d.nsx * d.nsy;
     pl->subs.resize(d.n_sub);
     std::vector<float> winx((size_t)d.n_sub * N, 0.f), winy((size_t)d.n_sub * N, 0.f);

@@ -285,3 +285,33 @@ def test_odd_R_at_256_matches_oracle(torch):
     v = o["valid"]
     assert np.array_equal(g["valid"], v)
     assert CS.rel_l2(g["out"][v], o["out"][v]) < IMG_TOL
+
+
+def test_paper_layout_matches_oracle(torch):
+    """The paper's own layout: full tiles only at stride N/4, merged by
+    their central stride x stride blocks (Sect. 3.2)."""
+    from paper_1701_00581_gb300 import SM_EDGE_DROP, SM_MOSAIC_CENTRAL, Channel, Plan
+    c = CS.case("ragged")
+    sp = c["spec"]
+    N, stride = c["N"], c["N"] // 4
+    plan = Plan(Channel(W=sp.W, H=sp.H, N=N, R=c["R"], stride=stride, fc=CS.FC, taper=c["taper"],
+                        max_frames=sp.F, edge_mode=SM_EDGE_DROP, mosaic_mode=SM_MOSAIC_CENTRAL))
+    b = CS.burst("ragged")
+    g = CS.gpu_run(plan, b["frames"], b["stf_emp"])
+    o = O.reconstruct_burst(b["frames"], N, stride, CS.FC, c["R"], c["taper"], b["stf_emp"], paper_layout=True)
+    assert plan.subfields().tolist() == [list(s) for s in o["subs"]]
+    assert np.array_equal(g["valid"], o["valid"])
+    v = o["valid"]
+    assert v.sum() == (len(set(s[0] for s in o["subs"])) * stride) * (len(set(s[1] for s in o["subs"])) * stride)
+    assert CS.rel_l2(g["out"][v], o["out"][v]) < IMG_TOL
+    assert np.all(g["out"][~v] == 0)
+
+
+def test_paper_layout_plan_of_the_tio_burst(torch):
+    from paper_1701_00581_gb300 import SM_EDGE_DROP, SM_MOSAIC_CENTRAL, Channel, Plan, SpeckleError
+    plan = Plan(Channel(W=2560, H=2160, N=256, R=24, stride=64, edge_mode=SM_EDGE_DROP,
+                        mosaic_mode=SM_MOSAIC_CENTRAL))
+    assert plan.info["n_sub"] == 1110 and plan.info["nsx"] == 37 and plan.info["nsy"] == 30
+    assert plan.info["n_cubes"] == 80
+    with pytest.raises(SpeckleError):          # the central mosaic needs full tiles
+        Plan(Channel(W=2560, H=2160, N=256, R=24, stride=64, mosaic_mode=SM_MOSAIC_CENTRAL))
