@@ -14,6 +14,8 @@ Weigelt 1977 and Lohmann, Weigelt & Wirnitzer 1983 for the bispectrum and
 the recursive phase).  Where the paper is silent the reading taken here is
 stated in each docstring:
 
+* flat/dark preprocessing (Table 2's first row): (raw - dark) / gain with
+  the gain (flat - dark) normalised to mean 1;
 * subfield grid (Sect. 2, Sect. 3.2): stride N/2, ``ceil((W-N)/s)+1`` tiles
   per axis, edge tiles keep their true extent and are zero-padded to N x N;
 * apodisation (silent): separable Tukey window, taper ``t`` px per edge;
@@ -52,6 +54,28 @@ import numpy as np
 W_BISPEC = 0     # phasor terms weighted by |B| (the plain sum of B's phasors)
 W_UNIT = 1       # unit-modulus phasor terms
 W_SNR = 2        # terms weighted by |B| / (P(u) P(v) P(w)), i.e. |B|^2 over its speckle-noise variance
+
+
+# ----------------------------------------------------------------------------
+# front end (Table 2: flat/dark preprocessing)
+# ----------------------------------------------------------------------------
+def calib_gain(flat: np.ndarray, dark: np.ndarray) -> np.ndarray:
+    """Normalised gain map of the detector: g = (flat - dark) / mean(flat - dark),
+    the mean over the pixels where flat > dark; g = 0 where flat <= dark
+    (dead pixels; reading: the paper names the step only)."""
+    d = np.asarray(flat, dtype=np.float64) - np.asarray(dark, dtype=np.float64)
+    live = d > 0
+    if not live.any():
+        raise ValueError("flat is nowhere above dark")
+    return np.where(live, d / d[live].mean(), 0.0)
+
+
+def calibrate(raw: np.ndarray, dark: np.ndarray, gain: np.ndarray) -> np.ndarray:
+    """Flat/dark correction of every frame: (raw - dark) / gain, 0 where gain = 0."""
+    raw = np.asarray(raw, dtype=np.float64)
+    g = np.asarray(gain, dtype=np.float64)
+    safe = np.where(g > 0, g, 1.0)
+    return np.where(g > 0, (raw - np.asarray(dark, dtype=np.float64)) / safe, 0.0)
 
 
 # ----------------------------------------------------------------------------

@@ -550,3 +550,29 @@ def test_mosaic_central_is_a_partition_by_nearest_centre():
                 i = owners[0]
                 x0, y0 = subs[i][:2]
                 assert out[py, px] == pytest.approx(i * 10000 + (py - y0) * 100 + (px - x0), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# front end (Table 2): flat/dark preprocessing
+# ---------------------------------------------------------------------------
+
+def test_flat_dark_recovers_the_scene():
+    rng = np.random.default_rng(21)
+    H, W = 37, 53
+    scene = rng.uniform(100.0, 3000.0, (4, H, W))
+    dark = rng.uniform(50.0, 80.0, (H, W))
+    g = rng.uniform(0.6, 1.4, (H, W))
+    flat = dark + 1000.0 * g
+    flat[3, 7] = dark[3, 7]                      # a dead pixel
+    raw = dark + scene * g
+    gain = O.calib_gain(flat, dark)
+    live = np.ones((H, W), bool)
+    live[3, 7] = False
+    assert gain[3, 7] == 0.0
+    assert gain[live].mean() == pytest.approx(1.0, rel=1e-14)
+    cal = O.calibrate(raw, dark, gain)
+    # (raw - dark) / gain = scene * g / (g / mean(g)) = scene * mean(g) over the live pixels
+    assert np.allclose(cal[:, live], scene[:, live] * g[live].mean(), rtol=1e-12)
+    assert np.all(cal[:, 3, 7] == 0.0)
+    with pytest.raises(ValueError):
+        O.calib_gain(dark, dark)
