@@ -23,6 +23,8 @@ stated in each docstring:
   mean-subtracted tile, each frame divided by its windowed flux, DC := 1;
 * power and mean spectrum (Sect. 3.2, Eq. 1 numerator), noise floor as the
   mean power in the half-plane corners of the (2K+1)^2 box outside the disk;
+* optional photon-noise bias removal from the bispectrum (Wirnitzer 1985),
+  the counts' photons per count given;
 * bispectrum (Sect. 2, Sect. 3.2; Weigelt 1977) on the pair domain
   D = {u in upper half plane, |u| <= r, 0 < |v| <= R, |u+v| <= r};
 * seeing (Sect. 3.1; von der Luehe 1984): D/r0 of every non-overlapping
@@ -330,6 +332,31 @@ def amplitude(P: np.ndarray, noise: float, stf: np.ndarray, N: int, fc: float) -
     A[T0 <= 0] = 0.0
     A[N // 2, N // 2] = 1.0
     return A
+
+
+def photon_terms(flux: np.ndarray, photon_gain: float) -> Tuple[float, float]:
+    """(<1/N_f>, <1/N_f^2>) over the frames, N_f = photon_gain * flux_f the
+    photon count of frame f's windowed tile."""
+    n = photon_gain * np.asarray(flux, dtype=np.float64)
+    return float(np.mean(1.0 / n)), float(np.mean(1.0 / (n * n)))
+
+
+def bispectrum_unbiased(B: np.ndarray, pairs: np.ndarray, P: np.ndarray, a1: float, a2: float) -> np.ndarray:
+    """Photon-noise bias removed from the mean bispectrum (Wirnitzer 1985).
+
+    For Poisson photon counts the triple product of a frame's normalised
+    spectrum has expectation B + (|I(u)|^2 + |I(v)|^2 + |I(u+v)|^2)/N - 2/N^2
+    (N the frame's photon count, |I|^2 each including its own 1/N); so
+    B_ub = B - (P(u) + P(v) + P(u+v)) <1/N> + 2 <1/N^2>, with P the measured
+    mean power (P(-k) = P(k)).  Reading: the window weights each photon by
+    w(x), and w^2 ~ w^3 ~ w is taken, as is the frame average of the
+    products as the product of the averages.
+    """
+    N = P.shape[0]
+    c = N // 2
+    ux, uy, vx, vy = pairs.T
+    wx, wy = ux + vx, uy + vy
+    return B - (P[uy + c, ux + c] + P[vy + c, vx + c] + P[wy + c, wx + c]) * a1 + 2.0 * a2
 
 
 # ----------------------------------------------------------------------------
@@ -734,7 +761,7 @@ def mosaic_central(recs: Sequence[np.ndarray], subs: Sequence[Tuple[int, int, in
 def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: int,
                          fc: float, R: int, taper: int, stf: np.ndarray,
                          weight: int = W_BISPEC, pairs: Optional[np.ndarray] = None,
-                         iters: int = 0) -> Dict:
+                         iters: int = 0, photon_gain: float = 0.0) -> Dict:
     """All steps for one subfield; returns every intermediate.  ``iters``
     least-squares sweeps (``phase_refine``) follow the recursion."""
     In, flux, mu = frame_spectra(frames, sub, N, taper)
@@ -743,6 +770,8 @@ def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: 
     if pairs is None:
         pairs = pair_domain(N, fc, R)
     B = bispectrum(In, pairs)
+    if photon_gain > 0:
+        B = bispectrum_unbiased(B, pairs, P, *photon_terms(flux, photon_gain))
     A = amplitude(P, noise, stf, N, fc)
     z = phase_recursion(B, pairs, M, N, fc, R, weight, P)
     if iters > 0:
@@ -755,7 +784,7 @@ def reconstruct_subfield(frames: np.ndarray, sub: Tuple[int, int, int, int], N: 
 def reconstruct_burst(frames: np.ndarray, N: int, stride: int, fc: float, R: int, taper: int,
                       stf: Optional[np.ndarray], weight: int = W_BISPEC,
                       subfields: Optional[Sequence[int]] = None, ck: float = 0.435,
-                      iters: int = 0, paper_layout: bool = False) -> Dict:
+                      iters: int = 0, paper_layout: bool = False, photon_gain: float = 0.0) -> Dict:
     """Whole burst: every subfield (or the listed ones), then the mosaic.
 
     With ``stf`` None the STF is the model at the seeing estimated from the
@@ -771,7 +800,7 @@ def reconstruct_burst(frames: np.ndarray, N: int, stride: int, fc: float, R: int
     subs = subfield_grid(W, H, N, stride, drop_edge=paper_layout)
     pairs = pair_domain(N, fc, R)
     pick = range(len(subs)) if subfields is None else subfields
-    results = {s: reconstruct_subfield(frames, subs[s], N, fc, R, taper, stf, weight, pairs, iters)
+    results = {s: reconstruct_subfield(frames, subs[s], N, fc, R, taper, stf, weight, pairs, iters, photon_gain)
                for s in pick}
     out = valid = None
     if subfields is None:
