@@ -96,6 +96,9 @@ typedef struct {
                            * see sm_stage_phase                               */
     int    edge_mode;     /* SM_EDGE_PAD / SM_EDGE_DROP                        */
     int    mosaic_mode;   /* SM_MOSAIC_BLEND / SM_MOSAIC_CENTRAL               */
+    double photon_gain;   /* photons per frame count; > 0 removes the photon-
+                           * noise bias from the bispectrum (see
+                           * sm_stage_bispectrum), 0 = off                   */
 } sm_channel;
 
 /* ======================================================================== *
@@ -176,6 +179,21 @@ int sm_workspace_query(const sm_plan* plan, int F, int nsub_chunk, sm_workspace_
  * length (<= nsub_chunk of the layout); per-chunk buffers start at the
  * chunk's first subfield, `rec` is indexed by absolute subfield.           */
 
+/* ---- front end (Table 2: flat/dark preprocessing), device pointers ----- */
+
+/* Normalised detector gain g = (flat - dark) / mean(flat - dark), the mean
+ * over the pixels where flat > dark (FP64, fixed order); g = 0 where
+ * flat <= dark.  flat, dark, gain: device float [H][W] of the plan's frame
+ * size.  Meant to run once per flat field (one CTA: about a millisecond
+ * for 2560 x 2160).                                                        */
+int sm_stage_gain(const sm_plan* plan, const float* flat, const float* dark, float* gain, void* stream);
+
+/* Flat/dark-corrected frames: out = (raw - dark) / g, 0 where g = 0.  raw:
+ * device [F][H][W] of frame_type; out: device float [F][H][W] (may not
+ * alias raw), which sm_stage_spectra / sm_reconstruct take as SM_F32.      */
+int sm_stage_calibrate(const sm_plan* plan, const void* raw, int frame_type, int F, const float* dark,
+                       const float* gain, float* out, void* stream);
+
 /* Sect. 2: cut, apodise, mean-subtract, 2-D DFT and normalise every frame
  * tile of subfields sub0..sub0+nsub-1.  frames: device [F][H][W] samples of
  * `frame_type`.  Writes spec, flux, mu.                                     */
@@ -214,7 +232,10 @@ int sm_stage_seeing_stf(const sm_plan* plan, void* ws, const sm_workspace_layout
 
 /* Sect. 2, 3.2 (speckle masking): mean bispectrum
  * B(w-v, v) = (1/F) sum_i I_i(w-v) I_i(v) conj I_i(w) on every pair the
- * phase recursion reads.                                                    */
+ * phase recursion reads.  With photon_gain > 0 the photon-noise bias is
+ * removed (Wirnitzer 1985): B - (P(w-v) + P(v) + P(w)) <1/N> + 2 <1/N^2>,
+ * N_f = photon_gain * flux_f the photon count of frame f's windowed tile,
+ * from this chunk's P (sm_stage_stats first) and flux.                      */
 int sm_stage_bispectrum(const sm_plan* plan, int F, int nsub, void* ws,
                         const sm_workspace_layout* lay, void* stream);
 

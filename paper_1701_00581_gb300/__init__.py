@@ -40,13 +40,14 @@ class Channel:
     phase_iters: int = 0
     edge_mode: int = SM_EDGE_PAD
     mosaic_mode: int = SM_MOSAIC_BLEND
+    photon_gain: float = 0.0
 
     def to_c(self) -> _lib.sm_channel:
         return _lib.sm_channel(
             self.W, self.H, self.N, self.stride if self.stride is not None else self.N // 2, self.R,
             self.fc, self.taper if self.taper is not None else self.N // 8, self.spectra_prec,
             self.phase_weight, self.ck, self.max_frames, self.acc_mode, self.phase_prec, self.phase_iters,
-            self.edge_mode, self.mosaic_mode)
+            self.edge_mode, self.mosaic_mode, self.photon_gain)
 
 
 def _ptr(t) -> Optional[int]:
@@ -164,6 +165,15 @@ class Plan:
         }
 
     # ---- stage entry points (device tensors) -------------------------------
+    def stage_gain(self, flat, dark, gain, stream=None):
+        """sm_stage_gain: normalised detector gain from a flat and a dark (device float [H][W])."""
+        check(self.lib.sm_stage_gain(self.h, _ptr(flat), _ptr(dark), _ptr(gain), _stream(stream)), "sm_stage_gain")
+
+    def stage_calibrate(self, raw, F, dark, gain, out, stream=None):
+        """sm_stage_calibrate: (raw - dark) / gain into float32 frames."""
+        check(self.lib.sm_stage_calibrate(self.h, _ptr(raw), _frame_type(raw), F, _ptr(dark), _ptr(gain), _ptr(out),
+                                          _stream(stream)), "sm_stage_calibrate")
+
     def stage_spectra(self, frames, F, sub0, nsub, ws, lay, stream=None):
         ft = SM_U16 if frames.dtype.__str__().endswith("uint16") else SM_F32
         check(self.lib.sm_stage_spectra(self.h, _ptr(frames), ft, F, sub0, nsub, _ptr(ws), C.byref(lay),

@@ -29,7 +29,7 @@ class sm_channel(C.Structure):
                 ("fc", C.c_double), ("taper", C.c_int), ("spectra_prec", C.c_int),
                 ("phase_weight", C.c_int), ("ck", C.c_double), ("max_frames", C.c_int),
                 ("acc_mode", C.c_int), ("phase_prec", C.c_int), ("phase_iters", C.c_int),
-                ("edge_mode", C.c_int), ("mosaic_mode", C.c_int)]
+                ("edge_mode", C.c_int), ("mosaic_mode", C.c_int), ("photon_gain", C.c_double)]
 
 
 class sm_plan_info(C.Structure):
@@ -75,6 +75,8 @@ SIGNATURES = {
     "sm_plan_cubes": (_I, [_P, _P]),
     "sm_plan_pair_index": (_I, [_P, C.c_longlong, _P, _P]),
     "sm_workspace_query": (_I, [_P, _I, _I, _LAY]),
+    "sm_stage_gain": (_I, [_P, _P, _P, _P, _P]),
+    "sm_stage_calibrate": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
     "sm_stage_spectra": (_I, [_P, _P, _I, _I, _I, _I, _P, _LAY, _P]),
     "sm_stage_stats": (_I, [_P, _I, _I, _P, _LAY, _P]),
     "sm_stage_amplitude": (_I, [_P, _I, _P, _P, _LAY, _P]),

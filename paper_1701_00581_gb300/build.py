@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libspeckle_gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["k_fft.cu", "k_small.cu", "k_bispec.cu", "k_phase.cu", "k_seeing.cu", "k_refine.cu", "sm_noalloc.cu"]
+CU_SOURCES = ["k_fft.cu", "k_small.cu", "k_bispec.cu", "k_phase.cu", "k_seeing.cu", "k_refine.cu", "k_front.cu", "sm_noalloc.cu"]
 CPP_SOURCES = ["sm_plan.cpp", "sm_api.cpp"]
 
 

@@ -145,6 +145,51 @@ __global__ void k_mosaic(PlanDev p, const float* __restrict__ rec, float* __rest
     if (valid) valid[(size_t)y * p.W + x] = ok ? 1 : 0;
 }
 
+// Photon-noise bias of the mean bispectrum (Wirnitzer 1985), removed in
+// place at every used pair of every tile: B -= (P(u) + P(v) + P(w)) <1/N>
+// - 2 <1/N^2> (real), u = w - v, P(-k) = P(k) from the half box, N_f the
+// photon count of frame f's windowed tile.  One CTA per (tile, subfield),
+// laid out as the bispectrum kernel's tiles.
+__global__ void __launch_bounds__(smi::BISPEC_THREADS)
+k_unbias(PlanDev p, int F, const float* __restrict__ flux, const float* __restrict__ P, float2* __restrict__ B) {
+    __shared__ float a12[2];
+    const int tile = blockIdx.x, sl = blockIdx.y;
+    const int4 T = p.tiles[tile];
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31, wyl = lane >> 2, gx = lane & 3;
+    const float* Ps = P + (size_t)sl * p.hb_rows * p.box_pitch;
+    if (threadIdx.x == 0) {             // <1/N_f>, <1/N_f^2>, N_f = photon_gain * flux_f
+        double a1 = 0.0, a2 = 0.0;
+        for (int f = 0; f < F; ++f) {
+            const double nf = p.photon_gain * (double)flux[(size_t)sl * F + f];
+            if (nf > 0.0) {
+                a1 += 1.0 / nf;
+                a2 += 1.0 / (nf * nf);
+            }
+        }
+        a12[0] = (float)(a1 / F);
+        a12[1] = (float)(a2 / F);
+    }
+    __syncthreads();
+    const float a1 = a12[0], a2 = a12[1];
+    float2* Bt = B + (size_t)(sl * p.n_tiles + tile) * smi::TILE_PAIRS;
+    auto pget = [&](int kx, int ky) -> float {
+        return ky >= 0 ? Ps[ky * p.box_pitch + kx + p.K] : Ps[(-ky) * p.box_pitch - kx + p.K];
+    };
+    const int wy = T.y + wyl, vy = T.w + q;
+    for (int j = 0; j < 4; ++j) {
+        const int wx = T.x + 4 * gx + j;
+        for (int kk = 0; kk < smi::VBX; ++kk) {
+            const int vx = T.z + kk;
+            const int w2 = wx * wx + wy * wy, v2 = vx * vx + vy * vy;
+            const int ux = wx - vx, uy = wy - vy, u2 = ux * ux + uy * uy;
+            const bool inH = wy > 0 || (wy == 0 && wx > 0);
+            if (!(inH && w2 >= 2 && w2 <= p.r2i && v2 > 0 && v2 <= p.R * p.R && v2 < w2 && u2 < w2)) continue;
+            float2& b = Bt[((wyl * smi::WBX + 4 * gx + j) * smi::TILE_V) + q * smi::VBX + kk];
+            b.x -= (pget(ux, uy) + pget(vx, vy) + pget(wx, wy)) * a1 - 2.f * a2;
+        }
+    }
+}
+
 }  // namespace
 
 namespace smk {
@@ -162,6 +207,12 @@ cudaError_t launch_amplitude(const smi::PlanDev& p, int nsub, const double* stf,
     const int ne = p.hb_rows * p.box_cols;
     dim3 grid((ne + 255) / 256, nsub);
     k_amplitude<<<grid, 256, 0, st>>>(p, stf, P, noise, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unbias(const smi::PlanDev& p, int F, int nsub, const float* flux, const float* P, float2* B,
+                          cudaStream_t st) {
+    k_unbias<<<dim3(p.n_tiles, nsub), smi::BISPEC_THREADS, 0, st>>>(p, F, flux, P, B);
     return cudaGetLastError();
 }
 

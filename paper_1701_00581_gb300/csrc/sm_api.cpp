@@ -100,6 +100,23 @@ extern "C" int sm_workspace_query(const sm_plan* plan, int F, int nsub_chunk, sm
     return SM_OK;
 }
 
+extern "C" int sm_stage_gain(const sm_plan* plan, const float* flat, const float* dark, float* gain, void* stream) {
+    if (!plan || !flat || !dark || !gain) { set_error("NULL argument"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_gain(plan->dev, flat, dark, gain, (cudaStream_t)stream), "gain kernel");
+}
+
+extern "C" int sm_stage_calibrate(const sm_plan* plan, const void* raw, int frame_type, int F, const float* dark,
+                                  const float* gain, float* out, void* stream) {
+    if (!plan || !raw || !dark || !gain || !out) { set_error("NULL argument"); return SM_EINVAL; }
+    if (frame_type != SM_U16 && frame_type != SM_F32) { set_error("bad frame_type"); return SM_EINVAL; }
+    if (F < 1) { set_error("F must be >= 1"); return SM_EINVAL; }
+    if ((const void*)out == raw) { set_error("out may not alias raw"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_calibrate(plan->dev, raw, frame_type, F, dark, gain, out, (cudaStream_t)stream),
+               "calibrate kernel");
+}
+
 extern "C" int sm_stage_spectra(const sm_plan* plan, const void* frames, int frame_type, int F, int sub0,
                                 int nsub, void* ws, const sm_workspace_layout* lay, void* stream) {
     int rc = check_lay(plan, ws, lay);
@@ -169,6 +186,15 @@ extern "C" int sm_stage_bispectrum(const sm_plan* plan, int F, int nsub, void* w
     if (rc) return rc;
     if (F < 1 || nsub < 1 || nsub > plan->dev.n_sub) { set_error("bad F or nsub"); return SM_EINVAL; }
     DeviceGuard g(plan->device);
+    if (plan->dev.photon_gain > 0.0) {
+        rc = ret(smk::launch_bispectrum(plan->dev, at<void>(ws, lay->spec), F, nsub, at<float2>(ws, lay->B),
+                                        (cudaStream_t)stream),
+                 "bispectrum kernel");
+        if (rc) return rc;
+        return ret(smk::launch_unbias(plan->dev, F, nsub, at<float>(ws, lay->flux), at<float>(ws, lay->P),
+                                      at<float2>(ws, lay->B), (cudaStream_t)stream),
+                   "photon-noise bias kernel");
+    }
     return ret(smk::launch_bispectrum(plan->dev, at<void>(ws, lay->spec), F, nsub, at<float2>(ws, lay->B),
                                       (cudaStream_t)stream),
                "bispectrum kernel");

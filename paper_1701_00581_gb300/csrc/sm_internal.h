@@ -47,6 +47,7 @@ struct PlanDev {
     int acc_mode, phase_prec;
     int phase_iters;         // least-squares sweeps after the recursion
     int mosaic_mode;         // SM_MOSAIC_BLEND / SM_MOSAIC_CENTRAL
+    double photon_gain;      // photons per count (> 0: photon-noise bias removal)
     const int* ref_start;    // [n_points + 1] CSR: refinement partial slots of each point
     const int* ref_idx;      //   tile * REF_SLOTS + slot, bit 31 = conjugate (lower-half occurrence)
     const int4* subs;        // [n_sub] x0, y0, w, h
@@ -91,10 +92,15 @@ cudaError_t launch_stats(const smi::PlanDev& p, const void* spec, int F, int nsu
                          float2* M, float* noise, cudaStream_t st);
 cudaError_t launch_amplitude(const smi::PlanDev& p, int nsub, const double* stf, const float* P,
                              const float* noise, float* A, cudaStream_t st);
+cudaError_t launch_gain(const smi::PlanDev& p, const float* flat, const float* dark, float* gain, cudaStream_t st);
+cudaError_t launch_calibrate(const smi::PlanDev& p, const void* raw, int frame_type, int F, const float* dark,
+                             const float* gain, float* out, cudaStream_t st);
 cudaError_t launch_seeing(const smi::PlanDev& p, int F, int sub0, int nsub, const float* P, const float2* M,
                           const float* noise, double* seeing, cudaStream_t st);
 cudaError_t launch_seeing_stf(const smi::PlanDev& p, double* seeing, double* stf, cudaStream_t st);
 int seeing_max_bins();   // annuli the seeing kernel holds in shared memory
+cudaError_t launch_unbias(const smi::PlanDev& p, int F, int nsub, const float* flux, const float* P, float2* B,
+                          cudaStream_t st);
 cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, int nsub,
                               float2* B, cudaStream_t st);
 cudaError_t launch_refine(const smi::PlanDev& p, int nsub, const float2* B, const float* P, double2* z,

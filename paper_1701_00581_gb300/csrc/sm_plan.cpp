@@ -73,6 +73,7 @@ int validate_channel(const sm_channel* ch) {
         set_error("acc_mode must be SM_ACC_PLAIN or SM_ACC_KAHAN"); return SM_EINVAL;
     }
     if (ch->phase_iters < 0 || ch->phase_iters > 64) { set_error("phase_iters must be in 0..64"); return SM_EINVAL; }
+    if (!(ch->photon_gain >= 0.0)) { set_error("photon_gain must be >= 0"); return SM_EINVAL; }
     if (ch->edge_mode != SM_EDGE_PAD && ch->edge_mode != SM_EDGE_DROP) {
         set_error("edge_mode must be SM_EDGE_PAD or SM_EDGE_DROP"); return SM_EINVAL;
     }
@@ -130,6 +131,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.acc_mode = ch->acc_mode; d.phase_prec = ch->phase_prec;
     d.phase_iters = ch->phase_iters;
     d.mosaic_mode = ch->mosaic_mode;
+    d.photon_gain = ch->photon_gain;
     d.box_rows = K + R + 1;
     d.box_cols = 2 * K + 1;
     d.box_pitch = (d.box_cols + 3) / 4 * 4;
