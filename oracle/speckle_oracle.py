@@ -16,6 +16,9 @@ stated in each docstring:
 
 * flat/dark preprocessing (Table 2's first row): (raw - dark) / gain with
   the gain (flat - dark) normalised to mean 1;
+* correlation tracking (Table 2): integer shifts maximising the cross-
+  correlation with a reference frame over a central window, applied with
+  the edges replicated;
 * subfield grid (Sect. 2, Sect. 3.2): stride N/2, ``ceil((W-N)/s)+1`` tiles
   per axis, edge tiles keep their true extent and are zero-padded to N x N;
 * apodisation (silent): separable Tukey window, taper ``t`` px per edge;
@@ -78,6 +81,55 @@ def calibrate(raw: np.ndarray, dark: np.ndarray, gain: np.ndarray) -> np.ndarray
     g = np.asarray(gain, dtype=np.float64)
     safe = np.where(g > 0, g, 1.0)
     return np.where(g > 0, (raw - np.asarray(dark, dtype=np.float64)) / safe, 0.0)
+
+
+def track_window(W: int, H: int, G: int, S: int) -> Tuple[int, int]:
+    """Origin (x0, y0) of the central G x G tracking window; the window moved
+    by any shift within +-S must stay inside the frame."""
+    x0, y0 = (W - G) // 2, (H - G) // 2
+    if G < 1 or S < 0 or x0 < S or y0 < S or x0 + G + S > W or y0 + G + S > H:
+        raise ValueError("tracking window plus search range does not fit the frame")
+    return x0, y0
+
+
+def track_shifts(frames: np.ndarray, ref: int, G: int, S: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Correlation tracking (Table 2): per frame the integer shift (sx, sy),
+    |sx|, |sy| <= S, maximising C(s) = sum over the central G x G window W
+    of a(x + s) (r(x) - mean_W r), r the reference frame; the first maximum
+    in the order sy = -S..S, then sx = -S..S.  Returns shifts [F][2] (sx, sy)
+    and C [F][2S+1][2S+1] (row sy + S, column sx + S).
+    (Readings: the paper names the step only; reference = one frame of the
+    burst, integer shifts.)"""
+    frames = np.asarray(frames, dtype=np.float64)
+    F, H, W = frames.shape
+    x0, y0 = track_window(W, H, G, S)
+    r = frames[ref, y0:y0 + G, x0:x0 + G]
+    r = r - r.mean()
+    C = np.zeros((F, 2 * S + 1, 2 * S + 1))
+    for f in range(F):
+        for sy in range(-S, S + 1):
+            for sx in range(-S, S + 1):
+                C[f, sy + S, sx + S] = np.sum(frames[f, y0 + sy:y0 + sy + G, x0 + sx:x0 + sx + G] * r)
+    shifts = np.zeros((F, 2), dtype=np.int64)
+    for f in range(F):
+        k = int(np.argmax(C[f]))                   # first maximum in row-major order
+        shifts[f] = (k % (2 * S + 1) - S, k // (2 * S + 1) - S)
+    return shifts, C
+
+
+def apply_shifts(frames: np.ndarray, shifts: np.ndarray) -> np.ndarray:
+    """Aligned frames out_f(x, y) = a_f(x + sx, y + sy), coordinates clamped
+    to the frame (edge pixels replicated; reading)."""
+    frames = np.asarray(frames, dtype=np.float64)
+    F, H, W = frames.shape
+    out = np.empty_like(frames)
+    ys, xs = np.arange(H), np.arange(W)
+    for f in range(F):
+        sx, sy = int(shifts[f][0]), int(shifts[f][1])
+        yy = np.clip(ys + sy, 0, H - 1)
+        xx = np.clip(xs + sx, 0, W - 1)
+        out[f] = frames[f][np.ix_(yy, xx)]
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -603,3 +603,25 @@ def test_photon_bias_removal_is_unbiased_for_poisson_frames():
     # photon_terms: <1/N> and <1/N^2> of the frames' photon counts
     a1, a2 = O.photon_terms(np.array([100.0, 400.0]), 2.0)
     assert a1 == pytest.approx((1 / 200 + 1 / 800) / 2) and a2 == pytest.approx((1 / 200 ** 2 + 1 / 800 ** 2) / 2)
+
+
+def test_correlation_tracking_recovers_known_shifts():
+    """Frames cut from one larger scene at known integer offsets: tracking
+    finds every offset, and the aligned frames equal the reference away
+    from the replicated edges."""
+    rng = np.random.default_rng(51)
+    big = S.make_object(160, 140, rng) * 1000.0
+    H, W, G, Sr = 100, 120, 48, 6
+    offs = [(0, 0), (3, -2), (-6, 5), (1, 6), (-4, -6)]
+    frames = np.stack([big[20 + dy:20 + dy + H, 20 + dx:20 + dx + W] for dx, dy in offs])
+    shifts, C = O.track_shifts(frames, 0, G, Sr)
+    assert shifts.tolist() == [[-dx, -dy] for dx, dy in offs]
+    assert C.shape == (5, 2 * Sr + 1, 2 * Sr + 1)
+    al = O.apply_shifts(frames, shifts)
+    m = Sr
+    assert np.array_equal(al[:, m:H - m, m:W - m], np.repeat(frames[:1, m:H - m, m:W - m], 5, axis=0))
+    # replicated edges: a shift past the border repeats the last row / column
+    one = O.apply_shifts(frames[:1], np.array([[W, H]]))
+    assert np.all(one[0] == frames[0, H - 1, W - 1])
+    with pytest.raises(ValueError):
+        O.track_shifts(frames, 0, 100, 6)
