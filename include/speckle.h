@@ -194,6 +194,24 @@ int sm_stage_gain(const sm_plan* plan, const float* flat, const float* dark, flo
 int sm_stage_calibrate(const sm_plan* plan, const void* raw, int frame_type, int F, const float* dark,
                        const float* gain, float* out, void* stream);
 
+/* Correlation tracking (Table 2): for every frame the integer shift
+ * (sx, sy), |sx|, |sy| <= S, maximising
+ * C(s) = sum over the central G x G window of a(x + s) (r(x) - mean r),
+ * r the frame `ref` of the burst, the first maximum in row-major (sy, sx)
+ * order (products in FP32 over 32-sample chunks, summed in FP64).
+ * ref_window: device float [G][G] scratch; cc: device double
+ * [F][2S+1][2S+1] receives C; shifts: device int [F][2] receives (sx, sy).
+ * SM_EINVAL unless 0 <= S <= 31 and the window moved by +-S fits the frame
+ * ((W-G)/2 >= S, (W-G)/2 + G + S <= W, and likewise in y).                */
+int sm_stage_track(const sm_plan* plan, const void* frames, int frame_type, int F, int ref, int G, int S,
+                   float* ref_window, double* cc, int* shifts, void* stream);
+
+/* Aligned frames: out_f(x, y) = a_f(x + sx_f, y + sy_f) with the
+ * coordinates clamped to the frame (edges replicated).  out: device float
+ * [F][H][W], not aliasing frames.                                          */
+int sm_stage_shift(const sm_plan* plan, const void* frames, int frame_type, int F, const int* shifts,
+                   float* out, void* stream);
+
 /* Sect. 2: cut, apodise, mean-subtract, 2-D DFT and normalise every frame
  * tile of subfields sub0..sub0+nsub-1.  frames: device [F][H][W] samples of
  * `frame_type`.  Writes spec, flux, mu.                                     */

@@ -174,6 +174,16 @@ class Plan:
         check(self.lib.sm_stage_calibrate(self.h, _ptr(raw), _frame_type(raw), F, _ptr(dark), _ptr(gain), _ptr(out),
                                           _stream(stream)), "sm_stage_calibrate")
 
+    def stage_track(self, frames, F, ref, G, S, ref_window, cc, shifts, stream=None):
+        """sm_stage_track: integer shifts (sx, sy) of every frame against frame `ref`."""
+        check(self.lib.sm_stage_track(self.h, _ptr(frames), _frame_type(frames), F, ref, G, S, _ptr(ref_window),
+                                      _ptr(cc), _ptr(shifts), _stream(stream)), "sm_stage_track")
+
+    def stage_shift(self, frames, F, shifts, out, stream=None):
+        """sm_stage_shift: frames shifted by their (sx, sy), edges replicated, into float32."""
+        check(self.lib.sm_stage_shift(self.h, _ptr(frames), _frame_type(frames), F, _ptr(shifts), _ptr(out),
+                                      _stream(stream)), "sm_stage_shift")
+
     def stage_spectra(self, frames, F, sub0, nsub, ws, lay, stream=None):
         ft = SM_U16 if frames.dtype.__str__().endswith("uint16") else SM_F32
         check(self.lib.sm_stage_spectra(self.h, _ptr(frames), ft, F, sub0, nsub, _ptr(ws), C.byref(lay),

@@ -77,6 +77,8 @@ SIGNATURES = {
     "sm_workspace_query": (_I, [_P, _I, _I, _LAY]),
     "sm_stage_gain": (_I, [_P, _P, _P, _P, _P]),
     "sm_stage_calibrate": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
+    "sm_stage_track": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "sm_stage_shift": (_I, [_P, _P, _I, _I, _P, _P, _P]),
     "sm_stage_spectra": (_I, [_P, _P, _I, _I, _I, _I, _P, _LAY, _P]),
     "sm_stage_stats": (_I, [_P, _I, _I, _P, _LAY, _P]),
     "sm_stage_amplitude": (_I, [_P, _I, _P, _P, _LAY, _P]),

@@ -117,6 +117,33 @@ extern "C" int sm_stage_calibrate(const sm_plan* plan, const void* raw, int fram
                "calibrate kernel");
 }
 
+extern "C" int sm_stage_track(const sm_plan* plan, const void* frames, int frame_type, int F, int ref, int G, int S,
+                              float* ref_window, double* cc, int* shifts, void* stream) {
+    if (!plan || !frames || !ref_window || !cc || !shifts) { set_error("NULL argument"); return SM_EINVAL; }
+    if (frame_type != SM_U16 && frame_type != SM_F32) { set_error("bad frame_type"); return SM_EINVAL; }
+    if (F < 1 || ref < 0 || ref >= F) { set_error("need F >= 1 and 0 <= ref < F"); return SM_EINVAL; }
+    const int W = plan->dev.W, H = plan->dev.H;
+    const int x0 = (W - G) / 2, y0 = (H - G) / 2;
+    if (S < 0 || S > smk::track_max_search() || G < 1 || x0 < S || y0 < S || x0 + G + S > W || y0 + G + S > H) {
+        set_error("tracking window plus search range does not fit the frame (or S > 31)"); return SM_EINVAL;
+    }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_track(plan->dev, frames, frame_type, F, ref, G, S, ref_window, cc, shifts,
+                                 (cudaStream_t)stream),
+               "tracking kernels");
+}
+
+extern "C" int sm_stage_shift(const sm_plan* plan, const void* frames, int frame_type, int F, const int* shifts,
+                              float* out, void* stream) {
+    if (!plan || !frames || !shifts || !out) { set_error("NULL argument"); return SM_EINVAL; }
+    if (frame_type != SM_U16 && frame_type != SM_F32) { set_error("bad frame_type"); return SM_EINVAL; }
+    if (F < 1) { set_error("F must be >= 1"); return SM_EINVAL; }
+    if ((const void*)out == frames) { set_error("out may not alias frames"); return SM_EINVAL; }
+    DeviceGuard g(plan->device);
+    return ret(smk::launch_shift(plan->dev, frames, frame_type, F, shifts, out, (cudaStream_t)stream),
+               "shift kernel");
+}
+
 extern "C" int sm_stage_spectra(const sm_plan* plan, const void* frames, int frame_type, int F, int sub0,
                                 int nsub, void* ws, const sm_workspace_layout* lay, void* stream) {
     int rc = check_lay(plan, ws, lay);

@@ -95,6 +95,11 @@ cudaError_t launch_amplitude(const smi::PlanDev& p, int nsub, const double* stf,
 cudaError_t launch_gain(const smi::PlanDev& p, const float* flat, const float* dark, float* gain, cudaStream_t st);
 cudaError_t launch_calibrate(const smi::PlanDev& p, const void* raw, int frame_type, int F, const float* dark,
                              const float* gain, float* out, cudaStream_t st);
+int track_max_search();   // largest search half-width S of the tracking kernel
+cudaError_t launch_track(const smi::PlanDev& p, const void* frames, int frame_type, int F, int ref, int G, int S,
+                         float* rw, double* cc, int* shifts, cudaStream_t st);
+cudaError_t launch_shift(const smi::PlanDev& p, const void* frames, int frame_type, int F, const int* shifts,
+                         float* out, cudaStream_t st);
 cudaError_t launch_seeing(const smi::PlanDev& p, int F, int sub0, int nsub, const float* P, const float2* M,
                           const float* noise, double* seeing, cudaStream_t st);
 cudaError_t launch_seeing_stf(const smi::PlanDev& p, double* seeing, double* stf, cudaStream_t st);

@@ -99,3 +99,41 @@ def test_photon_bias_removal_matches_oracle(torch):
     v = o["valid"]
     assert np.array_equal(g["valid"], v)
     assert CS.rel_l2(g["out"][v], o["out"][v]) < 1e-3
+
+
+@pytest.mark.parametrize("frame_type", ["u16", "f32"])
+def test_correlation_tracking_matches_oracle(torch, frame_type):
+    """Frames cut from one scene at known integer offsets: the GPU finds the
+    oracle's shifts (exactly), its correlation surface to 1e-3 of the peak,
+    and shifts the frames to the oracle's aligned frames (exactly: copies of
+    samples)."""
+    from paper_1701_00581_gb300 import Channel, Plan
+    from synth import burst as S
+    rng = np.random.default_rng(52)
+    big = S.make_object(360, 300, rng) * 2000.0
+    H, W, G, Sr = 200, 256, 128, 12
+    offs = [(0, 0), (5, -3), (-12, 7), (9, 12), (-7, -11), (12, -12), (0, 4), (-3, 0)]
+    frames = np.stack([big[40 + dy:40 + dy + H, 40 + dx:40 + dx + W] for dx, dy in offs])
+    frames = np.rint(frames).astype(np.uint16) if frame_type == "u16" else frames.astype(np.float32)
+    F = len(offs)
+    plan = Plan(Channel(W=W, H=H, N=64, R=8, max_frames=F))
+    dev = "cuda:0"
+    d_frames = torch.from_numpy(frames).to(dev)
+    rwin = torch.empty((G, G), dtype=torch.float32, device=dev)
+    cc = torch.empty((F, 2 * Sr + 1, 2 * Sr + 1), dtype=torch.float64, device=dev)
+    shifts = torch.empty((F, 2), dtype=torch.int32, device=dev)
+    plan.stage_track(d_frames, F, 0, G, Sr, rwin, cc, shifts)
+    out = torch.empty((F, H, W), dtype=torch.float32, device=dev)
+    plan.stage_shift(d_frames, F, shifts, out)
+    torch.cuda.synchronize()
+    sh_ref, C_ref = O.track_shifts(frames, 0, G, Sr)
+    assert shifts.cpu().numpy().tolist() == sh_ref.tolist() == [[-dx, -dy] for dx, dy in offs]
+    # FP32 products of ~2000-count samples with the zero-mean reference cancel
+    # ~1600-fold in each sum, so the surface agrees to ~1e-4 of its peak; the
+    # integer decision is exact because the peaks stand far above that
+    assert np.allclose(cc.cpu().numpy(), C_ref, rtol=0, atol=1e-3 * np.abs(C_ref).max())
+    al = O.apply_shifts(frames, sh_ref)
+    assert np.array_equal(out.cpu().numpy().astype(np.float64), al)
+    from paper_1701_00581_gb300 import SpeckleError
+    with pytest.raises(SpeckleError):
+        plan.stage_track(d_frames, F, 0, 240, Sr, rwin, cc, shifts)       # window + search exceed the frame
