@@ -161,7 +161,7 @@ __host__ __device__ constexpr size_t fft_smem(int N, int K) {
            + (size_t)N * sizeof(float2)                      // twiddles
            + (size_t)(K + 1) * sizeof(float2)                // window transform
            + (size_t)2 * N * sizeof(float)                   // windows
-           + (size_t)FFT_WARPS * 2 * sizeof(double);         // reductions
+           + (size_t)(FFT_WARPS * 2 + 2) * sizeof(double);   // reductions and scalars
 }
 
 // Spectra of one (frame, subfield): the tile times the window is transformed
@@ -236,17 +236,28 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
     }
     __syncthreads();
 
-    // windowed mean from the DC terms of the row transforms
-    double dacc = 0.0;
-    for (int y = tid; y < N; y += TS) dacc += (double)C[y].x;
+    // windowed mean from the DC terms of the row transforms: the warps
+    // holding DC terms reduce them, thread 0 forms the scalars once
+    if (tid < N) {
+        double dacc = 0.0;
+        for (int y = tid; y < N; y += TS) dacc += (double)C[y].x;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
-    if (lane == 0) red[warp] = dacc;
+        for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+        if (lane == 0) red[warp] = dacc;
+    }
     __syncthreads();
-    double tot = 0.0;
-    for (int i = 0; i < WS; ++i) tot += red[i];
-    const double wsum = p.winsum[s];
-    const float mean = (float)(tot / wsum);
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < (N < TS ? N : TS) / 32; ++i) tot += red[i];
+        const double wsum = p.winsum[s];
+        const float m = (float)(tot / wsum);
+        const double fl = (double)m * wsum;
+        red[WS] = fl;                                  // flux, then its reciprocal and the mean
+        reinterpret_cast<float*>(red + WS + 1)[0] = (float)(1.0 / fl);
+        reinterpret_cast<float*>(red + WS + 1)[1] = m;
+    }
+    __syncthreads();
+    const float mean = reinterpret_cast<const float*>(red + WS + 1)[1];
     // remove mean * window: row transform of w_x(x) w_y(y) mu is mu w_y(y) Wx(kx)
     for (int e = tid; e < K1 * h; e += TS) {
         const int kx = e / h, y = e - kx * h;
@@ -274,8 +285,8 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
     __syncthreads();
 
     // normalise by the windowed flux and store the box ky = -R..K
-    const double fl = (double)mean * wsum;
-    const float inv = (float)(1.0 / fl);
+    const double fl = red[WS];
+    const float inv = reinterpret_cast<const float*>(red + WS + 1)[0];
     const size_t base = ((size_t)sl * F + f) * p.box_rows * p.box_pitch;
     const int nbox = p.box_rows * p.box_cols;
     for (int e = tid; e < nbox; e += TS) {
