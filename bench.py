@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--weight", default="bispec", choices=["bispec", "unit", "snr"], help="phase-term weighting")
     ap.add_argument("--iters", type=int, default=0, help="least-squares phase sweeps after the recursion")
     ap.add_argument("--inflight", type=int, default=2, help="bursts in flight on the served e2e path")
+    ap.add_argument("--overlap", action="store_true",
+                    help="served paths: run admitted bursts' kernels concurrently instead of in submission order")
     ap.add_argument("--layout", default="overlap50", choices=["overlap50", "paper"],
                     help="overlap50: stride N/2, ragged edges padded, blended mosaic; paper: stride N/4, "
                          "full tiles only, central-block mosaic (1110 cubes, 2368x1920 for TiO)")
@@ -206,7 +208,7 @@ def kernel_traffic(kernel_file: str, units_per_launch: float):
 
 
 # ---------------------------------------------------------------------------- serving
-def serve_mixed(local, tio_burst, tio_ch, capacity, steps):
+def serve_mixed(local, tio_burst, tio_ch, capacity, steps, overlap=False):
     """Open-loop serving: Poisson arrivals of bursts from three NVST-shaped
     channels (TiO and G-band 2560x2160 with 256^2 subfields, H-alpha 1024^2
     with 128^2 subfields), admitted into the engine (120 GB budget) as slots
@@ -220,7 +222,7 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps):
     frames = [torch.from_numpy(tio_burst["frames"]).pin_memory(), None,
               torch.from_numpy(hb["frames"]).pin_memory()]
     frames[1] = frames[0]
-    eng = Engine(chans, hbm_budget_bytes=int(120e9), max_inflight=3, device=local)
+    eng = Engine(chans, hbm_budget_bytes=int(120e9), max_inflight=3, device=local, overlap_kernels=overlap)
     outs = {c: [torch.empty((chans[c].H, chans[c].W), dtype=torch.float32).pin_memory() for _ in range(3)]
             for c in range(3)}
     # warm up every channel once
@@ -264,7 +266,7 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps):
             "realised_arrival_rate": round(n / float(arrive[-1]), 3), "bursts": n, "channels": "TiO 2560x2160, G-band 2560x2160, H-alpha 1024x1024 (uniform mix)",
             "latency_ms_p50": round(1000 * float(np.percentile(lat, 50)), 1),
             "latency_ms_p99": round(1000 * float(np.percentile(lat, 99)), 1),
-            "nvst_rate_bursts_per_s": 0.3,
+            "nvst_rate_bursts_per_s": 0.3, "kernel_order": "concurrent" if overlap else "submission",
             "note": "Poisson arrivals at 60% of the measured e2e capacity; latency = arrival to mosaic on host"}
 
 
@@ -432,7 +434,8 @@ def main():
         K_IN = max(1, args.inflight)
         host_out = [torch.empty((spec.H, spec.W), dtype=torch.float32).pin_memory() for _ in range(K_IN)]
         host_valid = [torch.empty((spec.H, spec.W), dtype=torch.uint8).pin_memory() for _ in range(K_IN)]
-        eng = Engine([ch], hbm_budget_bytes=int(120e9), max_inflight=K_IN, device=local)
+        eng = Engine([ch], hbm_budget_bytes=int(120e9), max_inflight=K_IN, device=local,
+                     overlap_kernels=args.overlap)
         fr_np = host_frames.numpy()
 
         def serve(n):
@@ -464,11 +467,12 @@ def main():
                "d2h_bytes_per_step": int(spec.W * spec.H * 5),
                "latency_ms_p50": 1000 * float(np.percentile(lat, 50)),
                "latency_ms_p99": 1000 * float(np.percentile(lat, 99)),
-               "max_inflight": K_IN, "hbm_budget_gb": 120}
+               "max_inflight": K_IN, "hbm_budget_gb": 120,
+               "kernel_order": "concurrent" if args.overlap else "submission"}
 
     serving = None
     if not args.no_serve and args.workload == "tio2560" and not args.size:
-        serving = serve_mixed(local, b, ch, e2e["value"] if e2e else value, args.steps)
+        serving = serve_mixed(local, b, ch, e2e["value"] if e2e else value, args.steps, args.overlap)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -324,10 +324,12 @@ int sm_model_stf(const sm_channel* ch, int F, const double* d_over_r0, double* s
 
 /* ======================================================================== *
  *  Serving engine: bursts from several channels admitted as device slots   *
- *  free up, processed concurrently, results polled by ticket.  Each slot   *
- *  has its own stream; a burst's stage sequence is captured once as a CUDA *
- *  graph per (channel, F, frame type, arena offset, slot) and replayed for *
- *  later bursts with the same key.                                         *
+ *  free up, results polled by ticket.  Each slot has its own stream: one  *
+ *  burst's host-to-device copy overlaps another's kernels, and by default  *
+ *  the kernels themselves run one burst at a time in submission order     *
+ *  (overlap_kernels = 0).  A burst's stage sequence is captured once as a *
+ *  CUDA graph per (channel, F, frame type, STF mode, arena offset, slot)  *
+ *  and replayed for later bursts with the same key.                        *
  * ======================================================================== */
 typedef struct sm_handle sm_handle;
 
@@ -337,6 +339,11 @@ typedef struct {
     size_t            hbm_budget_bytes; /* device memory the engine may hold     */
     int               max_inflight;     /* bursts on the device at once (>= 1)   */
     int               device;
+    int               overlap_kernels;  /* 0: the kernels of admitted bursts run
+                                           in submission order, one burst at a
+                                           time, while the next bursts' frame
+                                           copies proceed on their own streams;
+                                           1: bursts' kernels run concurrently */
 } sm_config;
 
 typedef struct {

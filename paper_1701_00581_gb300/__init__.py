@@ -242,11 +242,12 @@ class Engine:
     """sm_open / sm_submit_burst / sm_poll / sm_close (the serving engine)."""
 
     def __init__(self, channels: Sequence[Channel], hbm_budget_bytes: int, max_inflight: int = 2,
-                 device: int = 0):
+                 device: int = 0, overlap_kernels: bool = False):
         self.lib = load()
         self._ch = (_lib.sm_channel * len(channels))(*[c.to_c() for c in channels])
         self.channels = list(channels)
-        cfg = _lib.sm_config(len(channels), self._ch, hbm_budget_bytes, max_inflight, device)
+        cfg = _lib.sm_config(len(channels), self._ch, hbm_budget_bytes, max_inflight, device,
+                             1 if overlap_kernels else 0)
         h = C.c_void_p()
         check(self.lib.sm_open(C.byref(cfg), C.byref(h)), "sm_open")
         self.h = h

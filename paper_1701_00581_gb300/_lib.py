@@ -48,7 +48,8 @@ class sm_workspace_layout(C.Structure):
 
 class sm_config(C.Structure):
     _fields_ = [("n_channels", C.c_int), ("ch", C.POINTER(sm_channel)),
-                ("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int), ("device", C.c_int)]
+                ("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int), ("device", C.c_int),
+                ("overlap_kernels", C.c_int)]
 
 
 class sm_burst(C.Structure):

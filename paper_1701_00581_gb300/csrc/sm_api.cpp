@@ -397,6 +397,14 @@ struct sm_handle {
     // fixed by that key, so a burst that lands where an earlier one did
     // replays its graph instead of issuing the launches again.
     std::map<std::tuple<int, int, size_t, int>, cudaGraphExec_t> graphs;
+    // Device order of the bursts' kernels (overlap_kernels == 0): re-recorded
+    // on the launching stream after every burst, and waited on by the next
+    // burst's stream before its graph, under launch_mu so that the wait,
+    // the launch and the record of one burst are not interleaved with
+    // another's.
+    cudaEvent_t order = nullptr;
+    bool ordered = false;                 // `order` has been recorded at least once
+    std::mutex launch_mu;
 };
 
 namespace {
@@ -511,6 +519,8 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
         return cuda_fail(e, "cudaMalloc(engine arena)");
     }
     h->arena.init(static_cast<char*>(h->dmem), cfg->hbm_budget_bytes);
+    e = cudaEventCreateWithFlags(&h->order, cudaEventDisableTiming);
+    if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaEventCreate"); }
     for (int i = 0; i < cfg->max_inflight; ++i) {
         cudaStream_t s;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -604,9 +614,22 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "staging burst");
     } else {
-        rc = launch_burst(h, b, j, d_frames, est ? nullptr : d_stf, ws, lay, st);
+        std::lock_guard<std::mutex> lk(h->launch_mu);
+        if (!h->cfg.overlap_kernels && h->ordered) {
+            // queue behind the previous burst's kernels; ev_start is taken
+            // again after the wait so that gpu_ms counts this burst's own
+            // kernels only
+            e = cudaStreamWaitEvent(st, h->order, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st);
+        }
+        if (e != cudaSuccess) rc = cuda_fail(e, "ordering burst");
+        else rc = launch_burst(h, b, j, d_frames, est ? nullptr : d_stf, ws, lay, st);
         if (rc == SM_OK) {
             e = cudaEventRecord(j.ev_done, st);
+            if (e == cudaSuccess && !h->cfg.overlap_kernels) {
+                e = cudaEventRecord(h->order, st);
+                h->ordered = e == cudaSuccess;
+            }
             if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
         }
     }
@@ -696,6 +719,7 @@ extern "C" int sm_close(sm_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     for (auto s : h->streams) cudaStreamDestroy(s);
+    if (h->order) cudaEventDestroy(h->order);
     for (auto p : h->stf_pinned) cudaFreeHost(p);
     if (h->dmem) cudaFree(h->dmem);
     for (auto* p : h->plans) sm_plan_destroy(p);

@@ -40,6 +40,36 @@ def test_binding_covers_header():
     assert sorted(_lib.SIGNATURES) == _header_functions()
 
 
+_STRUCTS = ["sm_channel", "sm_plan_info", "sm_workspace_layout", "sm_config", "sm_burst", "sm_result"]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes mirror has the C compiler's size and field offsets for
+    the header's struct (a field added on one side only shifts the rest)."""
+    import shutil
+    import subprocess
+    from paper_1701_00581_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "speckle.h"', "int main(void) {"]
+    expect = []
+    for name in _STRUCTS:
+        cls = getattr(_lib, name)
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(C.sizeof(cls))
+        for f in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {f[0]}));')
+            expect.append(getattr(cls, f[0]).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
+
+
 def test_strerror(lib):
     assert lib.sm_strerror(0) == b"ok"
     assert lib.sm_strerror(-3) == b"no free slot, retry later"

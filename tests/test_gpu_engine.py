@@ -58,13 +58,15 @@ def test_engine_matches_plain_path(torch):
     assert np.array_equal(out, ref_out)
 
 
-def test_alone_equals_in_the_mix(torch):
+@pytest.mark.parametrize("overlap", [False, True])
+def test_alone_equals_in_the_mix(torch, overlap):
     """Bursts admitted while others are on the device give the same mosaic
-    (bitwise) as each burst served alone."""
+    (bitwise) as each burst served alone, with the bursts' kernels run in
+    submission order or concurrently."""
     from paper_1701_00581_gb300 import Engine
     ch = CS.gpu_channel("ragged")
     bursts = _bursts(4)
-    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=3)
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=3, overlap_kernels=overlap)
     alone = [_serve_one(eng, b, 110, 150) for b in bursts]
     outs = [np.zeros((110, 150), np.float32) for _ in bursts]
     pending, k = [], 0
@@ -81,6 +83,24 @@ def test_alone_equals_in_the_mix(torch):
     eng.close()
     for (o, _), m in zip(alone, outs):
         assert np.array_equal(o, m)
+
+
+def test_ordered_bursts_finish_in_submission_order(torch):
+    """With overlap_kernels off, a burst's kernels start after the previous
+    burst's have finished: once the last ticket is done, every earlier one
+    is done too (a non-blocking poll finds it complete)."""
+    from paper_1701_00581_gb300 import Engine
+    ch = CS.gpu_channel("ragged")
+    bursts = _bursts(3)
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=3)
+    outs = [np.zeros((110, 150), np.float32) for _ in bursts]
+    tickets = [eng.submit(0, b["frames"], o, d_over_r0=b["d_over_r0"]) for b, o in zip(bursts, outs)]
+    st, res = eng.poll(tickets[-1], -1)
+    assert st == 0 and res["gpu_ms"] > 0
+    for t in tickets[:-1]:
+        st, res = eng.poll(t, 0)
+        assert st == 0 and res is not None
+    eng.close()
 
 
 def test_two_channels_in_one_engine(torch):
