@@ -438,6 +438,8 @@ def main():
                      overlap_kernels=args.overlap)
         fr_np = host_frames.numpy()
 
+        stages = []
+
         def serve(n):
             pending, lat = [], []
             submitted = done = 0
@@ -451,12 +453,14 @@ def main():
                     pending.append((tk, time.perf_counter()))
                     submitted += 1
                 tk, ts = pending.pop(0)
-                eng.poll(tk, -1)
+                _, res = eng.poll(tk, -1)
                 lat.append(time.perf_counter() - ts)
+                stages.append(res["stage_ms"])
                 done += 1
             return time.perf_counter() - t_start, lat
 
         serve(max(1, args.warmup))
+        stages.clear()
         if world > 1:
             dist.barrier()
         el, lat = serve(args.steps)
@@ -468,7 +472,8 @@ def main():
                "latency_ms_p50": 1000 * float(np.percentile(lat, 50)),
                "latency_ms_p99": 1000 * float(np.percentile(lat, 99)),
                "max_inflight": K_IN, "hbm_budget_gb": 120,
-               "kernel_order": "concurrent" if args.overlap else "submission"}
+               "kernel_order": "concurrent" if args.overlap else "submission",
+               "stage_ms": {k: round(float(np.mean([st[k] for st in stages])), 3) for k in stages[0]}}
 
     serving = None
     if not args.no_serve and args.workload == "tio2560" and not args.size:

@@ -344,6 +344,16 @@ typedef struct {
                                            time, while the next bursts' frame
                                            copies proceed on their own streams;
                                            1: bursts' kernels run concurrently */
+    /* Optional device allocator for the engine's one arena of
+     * hbm_budget_bytes (both NULL: cudaMalloc / cudaFree).  dev_alloc is
+     * called once by sm_open and must return device memory of `device`
+     * aligned to 256 bytes, or NULL (sm_open then fails with SM_ENOMEM);
+     * dev_free is called once by sm_close (or by a failing sm_open) with
+     * that pointer.  Both receive alloc_ctx.  Giving one without the other
+     * is SM_EINVAL.                                                          */
+    void*           (*dev_alloc)(size_t bytes, void* ctx);
+    void            (*dev_free)(void* ptr, void* ctx);
+    void*             alloc_ctx;
 } sm_config;
 
 typedef struct {
@@ -368,6 +378,11 @@ typedef struct {
     size_t bytes_admitted;              /* device bytes held by the burst         */
     double d_over_r0;                   /* the burst's estimated D / mean r0, or 0
                                          * when the STF or D/r0 was given         */
+    double stage_ms[8];                 /* device time of each stage, summed over
+                                         * chunks: spectra, P/M/noise, seeing
+                                         * estimate (0 when not estimated),
+                                         * modulus, bispectrum, phase, inverse,
+                                         * mosaic                                 */
 } sm_result;
 
 int sm_open(const sm_config* cfg, sm_handle** out);

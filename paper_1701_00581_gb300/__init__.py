@@ -238,16 +238,42 @@ def _frame_type(frames) -> int:
     return SM_U16 if str(frames.dtype).endswith("uint16") else SM_F32
 
 
+# sm_result.stage_ms, in order
+STAGE_NAMES = ("spectra", "stats", "seeing", "modulus", "bispectrum", "phase", "inverse", "mosaic")
+
+
 class Engine:
     """sm_open / sm_submit_burst / sm_poll / sm_close (the serving engine)."""
 
     def __init__(self, channels: Sequence[Channel], hbm_budget_bytes: int, max_inflight: int = 2,
-                 device: int = 0, overlap_kernels: bool = False):
+                 device: int = 0, overlap_kernels: bool = False, allocator: Optional[str] = None):
+        """``allocator="torch"`` takes the engine's arena from torch's caching
+        allocator (one uint8 tensor held until close) instead of cudaMalloc."""
         self.lib = load()
         self._ch = (_lib.sm_channel * len(channels))(*[c.to_c() for c in channels])
         self.channels = list(channels)
+        self._arena: Dict[int, object] = {}
+        alloc, free = _lib.DEV_ALLOC(), _lib.DEV_FREE()    # NULL: cudaMalloc / cudaFree
+        if allocator == "torch":
+            import torch
+
+            def _alloc(nbytes, _ctx):
+                try:
+                    t = torch.empty(int(nbytes), dtype=torch.uint8, device=f"cuda:{device}")
+                except RuntimeError:
+                    return None
+                self._arena[t.data_ptr()] = t
+                return t.data_ptr()
+
+            def _free(ptr, _ctx):
+                self._arena.pop(ptr, None)
+
+            alloc, free = _lib.DEV_ALLOC(_alloc), _lib.DEV_FREE(_free)
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
+        self._callbacks = (alloc, free)          # kept alive while the engine holds them
         cfg = _lib.sm_config(len(channels), self._ch, hbm_budget_bytes, max_inflight, device,
-                             1 if overlap_kernels else 0)
+                             1 if overlap_kernels else 0, alloc, free, None)
         h = C.c_void_p()
         check(self.lib.sm_open(C.byref(cfg), C.byref(h)), "sm_open")
         self.h = h
@@ -286,7 +312,8 @@ class Engine:
         check(st, "sm_poll")
         self._keep.pop(ticket, None)
         return st, {"t_submit_ms": res.t_submit_ms, "t_done_ms": res.t_done_ms, "gpu_ms": res.gpu_ms,
-                    "bytes_admitted": res.bytes_admitted, "d_over_r0": res.d_over_r0}
+                    "bytes_admitted": res.bytes_admitted, "d_over_r0": res.d_over_r0,
+                    "stage_ms": dict(zip(STAGE_NAMES, list(res.stage_ms)))}
 
     def close(self):
         if self.h:

@@ -46,10 +46,15 @@ class sm_workspace_layout(C.Structure):
                  "bytes")]
 
 
+DEV_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class sm_config(C.Structure):
     _fields_ = [("n_channels", C.c_int), ("ch", C.POINTER(sm_channel)),
                 ("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int), ("device", C.c_int),
-                ("overlap_kernels", C.c_int)]
+                ("overlap_kernels", C.c_int), ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE),
+                ("alloc_ctx", C.c_void_p)]
 
 
 class sm_burst(C.Structure):
@@ -60,7 +65,8 @@ class sm_burst(C.Structure):
 
 class sm_result(C.Structure):
     _fields_ = [("status", C.c_int), ("t_submit_ms", C.c_double), ("t_done_ms", C.c_double),
-                ("gpu_ms", C.c_double), ("bytes_admitted", C.c_size_t), ("d_over_r0", C.c_double)]
+                ("gpu_ms", C.c_double), ("bytes_admitted", C.c_size_t), ("d_over_r0", C.c_double),
+                ("stage_ms", C.c_double * 8)]
 
 
 _P = C.c_void_p

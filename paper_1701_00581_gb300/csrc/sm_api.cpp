@@ -1,6 +1,7 @@
 // C ABI: workspace layout, stage entry points, the whole-burst path and the
 // serving engine.  No exception crosses the ABI; every call returns a status.
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <chrono>
@@ -264,51 +265,120 @@ extern "C" int sm_stage_mosaic(const sm_plan* plan, void* ws, const sm_workspace
                "mosaic kernel");
 }
 
-extern "C" int sm_reconstruct(const sm_plan* plan, const void* frames, int frame_type, int F,
-                              const double* stf, int nsub_chunk, void* ws, const sm_workspace_layout* lay,
-                              float* out, uint8_t* valid, void* stream) {
+namespace {
+
+// One stage launch of a whole-burst reconstruction: which stage, over which
+// subfields.  The reconstruction is this list run in order on one stream.
+enum StageId { ST_SPECTRA, ST_STATS, ST_SEEING, ST_SEEING_STF, ST_AMPLITUDE, ST_BISPECTRUM, ST_PHASE,
+               ST_INVERSE, ST_MOSAIC };
+struct StageCall {
+    StageId stage;
+    int s0, ns;
+};
+
+// Reported stage of each StageId (sm_result.stage_ms): the seeing estimate
+// and its STF table count as one stage.
+int reported_stage(StageId s) {
+    static const int map[] = {0, 1, 2, 2, 3, 4, 5, 6, 7};
+    return map[s];
+}
+
+// The stage sequence of sm_reconstruct.  Seeing from the burst itself
+// (Sect. 3.1) when no STF is given: with one chunk the cubes are estimated
+// inside it; otherwise a first pass over the chunks holding cubes estimates
+// them before any modulus is formed.
+std::vector<StageCall> burst_schedule(const sm_plan* plan, bool est, int nsub_chunk) {
+    std::vector<StageCall> c;
+    const int n = plan->dev.n_sub;
+    if (est && nsub_chunk < n) {
+        for (int s0 = 0; s0 < n; s0 += nsub_chunk) {
+            const int ns = std::min(nsub_chunk, n - s0);
+            bool cubes = false;
+            for (int s = s0; s < s0 + ns; ++s) cubes |= plan->cube_of_sub[s] >= 0;
+            if (!cubes) continue;
+            c.push_back({ST_SPECTRA, s0, ns});
+            c.push_back({ST_STATS, s0, ns});
+            c.push_back({ST_SEEING, s0, ns});
+        }
+        c.push_back({ST_SEEING_STF, 0, 0});
+    }
+    for (int s0 = 0; s0 < n; s0 += nsub_chunk) {
+        const int ns = std::min(nsub_chunk, n - s0);
+        c.push_back({ST_SPECTRA, s0, ns});
+        c.push_back({ST_STATS, s0, ns});
+        if (est && nsub_chunk >= n) {
+            c.push_back({ST_SEEING, s0, ns});
+            c.push_back({ST_SEEING_STF, 0, 0});
+        }
+        c.push_back({ST_AMPLITUDE, s0, ns});
+        c.push_back({ST_BISPECTRUM, s0, ns});
+        c.push_back({ST_PHASE, s0, ns});
+        c.push_back({ST_INVERSE, s0, ns});
+    }
+    c.push_back({ST_MOSAIC, 0, n});
+    return c;
+}
+
+// Checks of sm_reconstruct's arguments; on success *stf_used is the STF
+// table the amplitude stage reads (the workspace's own when estimated).
+int reconstruct_check(const sm_plan* plan, int F, const double* stf, int nsub_chunk, void* ws,
+                      const sm_workspace_layout* lay, const double** stf_used) {
     int rc = check_lay(plan, ws, lay);
     if (rc) return rc;
     const int n = plan->dev.n_sub;
     if (nsub_chunk < 1 || nsub_chunk > n) { set_error("nsub_chunk out of range"); return SM_EINVAL; }
-    // Seeing from the burst itself (Sect. 3.1) when no STF is given: with one
-    // chunk the cubes are estimated inside it; otherwise a first pass over
-    // the chunks holding cubes estimates them before any modulus is formed.
-    const bool est = stf == nullptr;
-    if (est) {
+    *stf_used = stf;
+    if (stf == nullptr) {
         if (plan->dev.n_cubes < 1) {
             set_error("no STF given and no seeing cube to estimate it (the stride must divide N)");
             return SM_EINVAL;
         }
         if (F < 2) { set_error("no STF given and F < 2: the seeing estimate needs two frames"); return SM_EINVAL; }
-        stf = at<double>(ws, lay->stf);
-        if (nsub_chunk < n) {
-            for (int s0 = 0; s0 < n; s0 += nsub_chunk) {
-                const int ns = std::min(nsub_chunk, n - s0);
-                bool cubes = false;
-                for (int s = s0; s < s0 + ns; ++s) cubes |= plan->cube_of_sub[s] >= 0;
-                if (!cubes) continue;
-                if ((rc = sm_stage_spectra(plan, frames, frame_type, F, s0, ns, ws, lay, stream))) return rc;
-                if ((rc = sm_stage_stats(plan, F, ns, ws, lay, stream))) return rc;
-                if ((rc = sm_stage_seeing(plan, F, s0, ns, ws, lay, stream))) return rc;
-            }
-            if ((rc = sm_stage_seeing_stf(plan, ws, lay, stream))) return rc;
-        }
+        *stf_used = at<double>(ws, lay->stf);
     }
-    for (int s0 = 0; s0 < n; s0 += nsub_chunk) {
-        const int ns = std::min(nsub_chunk, n - s0);
-        if ((rc = sm_stage_spectra(plan, frames, frame_type, F, s0, ns, ws, lay, stream))) return rc;
-        if ((rc = sm_stage_stats(plan, F, ns, ws, lay, stream))) return rc;
-        if (est && nsub_chunk >= n) {
-            if ((rc = sm_stage_seeing(plan, F, s0, ns, ws, lay, stream))) return rc;
-            if ((rc = sm_stage_seeing_stf(plan, ws, lay, stream))) return rc;
+    return SM_OK;
+}
+
+// Run a schedule; with `marks`, marks[i] is recorded on the stream before
+// call i and marks[calls.size()] after the last (timing of each call).
+int run_schedule(const sm_plan* plan, const std::vector<StageCall>& calls, const void* frames, int frame_type,
+                 int F, const double* stf, void* ws, const sm_workspace_layout* lay, float* out, uint8_t* valid,
+                 void* stream, const std::vector<cudaEvent_t>* marks) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto mark = [&](size_t i) -> int {
+        if (!marks) return SM_OK;
+        return ret(cudaEventRecordWithFlags((*marks)[i], st, cudaEventRecordExternal), "cudaEventRecordWithFlags");
+    };
+    int rc = SM_OK;
+    for (size_t i = 0; i < calls.size(); ++i) {
+        const StageCall& c = calls[i];
+        if ((rc = mark(i))) return rc;
+        switch (c.stage) {
+        case ST_SPECTRA: rc = sm_stage_spectra(plan, frames, frame_type, F, c.s0, c.ns, ws, lay, stream); break;
+        case ST_STATS: rc = sm_stage_stats(plan, F, c.ns, ws, lay, stream); break;
+        case ST_SEEING: rc = sm_stage_seeing(plan, F, c.s0, c.ns, ws, lay, stream); break;
+        case ST_SEEING_STF: rc = sm_stage_seeing_stf(plan, ws, lay, stream); break;
+        case ST_AMPLITUDE: rc = sm_stage_amplitude(plan, c.ns, stf, ws, lay, stream); break;
+        case ST_BISPECTRUM: rc = sm_stage_bispectrum(plan, F, c.ns, ws, lay, stream); break;
+        case ST_PHASE: rc = sm_stage_phase(plan, c.ns, ws, lay, stream); break;
+        case ST_INVERSE: rc = sm_stage_inverse(plan, F, c.s0, c.ns, ws, lay, stream); break;
+        case ST_MOSAIC: rc = sm_stage_mosaic(plan, ws, lay, out, valid, stream); break;
         }
-        if ((rc = sm_stage_amplitude(plan, ns, stf, ws, lay, stream))) return rc;
-        if ((rc = sm_stage_bispectrum(plan, F, ns, ws, lay, stream))) return rc;
-        if ((rc = sm_stage_phase(plan, ns, ws, lay, stream))) return rc;
-        if ((rc = sm_stage_inverse(plan, F, s0, ns, ws, lay, stream))) return rc;
+        if (rc) return rc;
     }
-    return sm_stage_mosaic(plan, ws, lay, out, valid, stream);
+    return mark(calls.size());
+}
+
+}  // namespace
+
+extern "C" int sm_reconstruct(const sm_plan* plan, const void* frames, int frame_type, int F,
+                              const double* stf, int nsub_chunk, void* ws, const sm_workspace_layout* lay,
+                              float* out, uint8_t* valid, void* stream) {
+    const double* stf_used = nullptr;
+    int rc = reconstruct_check(plan, F, stf, nsub_chunk, ws, lay, &stf_used);
+    if (rc) return rc;
+    return run_schedule(plan, burst_schedule(plan, stf == nullptr, nsub_chunk), frames, frame_type, F, stf_used,
+                        ws, lay, out, valid, stream, nullptr);
 }
 
 // ============================================================================
@@ -372,6 +442,8 @@ struct Job {
     uint8_t* d_valid = nullptr;
     const double* d_seeing = nullptr;     // the burst's D / mean r0 when estimated
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    const std::vector<cudaEvent_t>* marks = nullptr;   // the burst graph's stage marks
+    const std::vector<int>* mark_stage = nullptr;
     double t_submit = 0.0;
     int status = SM_PENDING;
 };
@@ -396,7 +468,12 @@ struct sm_handle {
     // arena offset, stream slot): every pointer a burst's kernels take is
     // fixed by that key, so a burst that lands where an earlier one did
     // replays its graph instead of issuing the launches again.
-    std::map<std::tuple<int, int, size_t, int>, cudaGraphExec_t> graphs;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<cudaEvent_t> marks;   // recorded before each stage call and after the last
+        std::vector<int> stage;           // reported stage of each call
+    };
+    std::map<std::tuple<int, int, size_t, int>, Graph> graphs;
     // Device order of the bursts' kernels (overlap_kernels == 0): re-recorded
     // on the launching stream after every burst, and waited on by the next
     // burst's stream before its graph, under launch_mu so that the wait,
@@ -449,35 +526,50 @@ namespace {
 // CUDA graph (captured on first use of the key).  The frame type and the
 // STF mode (given, or estimated on the device when d_stf is NULL) are part
 // of the captured kernels, so they join the key through the F slot.
-int launch_burst(sm_handle* h, const sm_burst* b, const Job& j, const void* d_frames, const double* d_stf,
+int launch_burst(sm_handle* h, const sm_burst* b, Job& j, const void* d_frames, const double* d_stf,
                  void* ws, sm_workspace_layout& lay, cudaStream_t st) {
     const auto key = std::make_tuple(b->channel, b->F * 4 + (d_stf ? 0 : 2) + (b->frame_type == SM_F32 ? 1 : 0),
                                      j.off, j.slot);
-    cudaGraphExec_t exec = nullptr;
+    sm_handle::Graph* g = nullptr;
     {
         std::lock_guard<std::mutex> lk(h->mu);
         auto it = h->graphs.find(key);
-        if (it != h->graphs.end()) exec = it->second;
+        if (it != h->graphs.end()) g = &it->second;
     }
-    if (!exec) {
+    if (!g) {
+        const sm_plan* plan = h->plans[b->channel];
+        const double* stf_used = nullptr;
+        int rc = reconstruct_check(plan, b->F, d_stf, h->chunk[b->channel], ws, &lay, &stf_used);
+        if (rc) return rc;
+        const std::vector<StageCall> calls = burst_schedule(plan, d_stf == nullptr, h->chunk[b->channel]);
+        sm_handle::Graph ng;
+        for (const StageCall& c : calls) ng.stage.push_back(reported_stage(c.stage));
+        ng.marks.assign(calls.size() + 1, nullptr);
+        auto drop = [&](cudaGraph_t graph) {
+            if (graph) cudaGraphDestroy(graph);
+            for (auto ev : ng.marks) if (ev) cudaEventDestroy(ev);
+        };
+        for (auto& ev : ng.marks) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) { drop(nullptr); return cuda_fail(e, "cudaEventCreate"); }
+        }
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        const int rc = sm_reconstruct(h->plans[b->channel], d_frames, b->frame_type, b->F, d_stf,
-                                      h->chunk[b->channel], ws, &lay, j.d_out, j.d_valid, st);
+        if (e != cudaSuccess) { drop(nullptr); return cuda_fail(e, "cudaStreamBeginCapture"); }
+        rc = run_schedule(plan, calls, d_frames, b->frame_type, b->F, stf_used, ws, &lay, j.d_out, j.d_valid, st,
+                          &ng.marks);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(st, &graph);
-        if (rc != SM_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (rc != SM_OK) { drop(graph); return rc; }
+        if (e != cudaSuccess) { drop(graph); return cuda_fail(e, "cudaStreamEndCapture"); }
+        e = cudaGraphInstantiate(&ng.exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (e != cudaSuccess) { drop(nullptr); return cuda_fail(e, "cudaGraphInstantiate"); }
         std::lock_guard<std::mutex> lk(h->mu);
-        h->graphs[key] = exec;
+        g = &(h->graphs[key] = std::move(ng));
     }
-    return ret(cudaGraphLaunch(exec, st), "cudaGraphLaunch");
+    j.marks = &g->marks;
+    j.mark_stage = &g->stage;
+    return ret(cudaGraphLaunch(g->exec, st), "cudaGraphLaunch");
 }
 
 }  // namespace
@@ -485,6 +577,9 @@ int launch_burst(sm_handle* h, const sm_burst* b, const Job& j, const void* d_fr
 extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
     if (!cfg || !out || cfg->n_channels < 1 || !cfg->ch || cfg->max_inflight < 1) {
         set_error("bad sm_config"); return SM_EINVAL;
+    }
+    if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) {
+        set_error("dev_alloc and dev_free must be given together"); return SM_EINVAL;
     }
     *out = nullptr;
     sm_handle* h = new (std::nothrow) sm_handle();
@@ -512,7 +607,20 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
         }
         h->chunk[c] = lo;
     }
-    cudaError_t e = cudaMalloc(&h->dmem, cfg->hbm_budget_bytes);
+    cudaError_t e = cudaSuccess;
+    if (cfg->dev_alloc) {
+        h->dmem = cfg->dev_alloc(cfg->hbm_budget_bytes, cfg->alloc_ctx);
+        if (!h->dmem || (reinterpret_cast<uintptr_t>(h->dmem) & 255)) {
+            if (h->dmem) cfg->dev_free(h->dmem, cfg->alloc_ctx);
+            h->dmem = nullptr;
+            for (auto* q : h->plans) sm_plan_destroy(q);
+            delete h;
+            set_error("dev_alloc returned NULL or a pointer not aligned to 256 bytes");
+            return SM_ENOMEM;
+        }
+    } else {
+        e = cudaMalloc(&h->dmem, cfg->hbm_budget_bytes);
+    }
     if (e != cudaSuccess) {
         for (auto* q : h->plans) sm_plan_destroy(q);
         delete h;
@@ -693,6 +801,13 @@ extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result*
     if (e == cudaSuccess && j.d_seeing) e = cudaMemcpy(&dr0, j.d_seeing, sizeof(double), cudaMemcpyDeviceToHost);
     float gms = 0.f;
     cudaEventElapsedTime(&gms, j.ev_start, j.ev_done);
+    double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (j.marks)
+        for (size_t i = 0; i + 1 < j.marks->size(); ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, (*j.marks)[i], (*j.marks)[i + 1]) == cudaSuccess)
+                stage_ms[(*j.mark_stage)[i]] += ms;
+        }
     int rc = e == cudaSuccess ? SM_OK : cuda_fail(e, "copying the mosaic");
     if (res) {
         res->status = rc;
@@ -701,6 +816,7 @@ extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result*
         res->gpu_ms = gms;
         res->bytes_admitted = j.bytes;
         res->d_over_r0 = dr0;
+        for (int i = 0; i < 8; ++i) res->stage_ms[i] = stage_ms[i];
     }
     finish_job(h, j);
     h->jobs.erase(it);
@@ -716,12 +832,18 @@ extern "C" int sm_close(sm_handle* h) {
         for (auto& kv : h->jobs) finish_job(h, kv.second);
         h->jobs.clear();
     }
-    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : h->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        for (auto ev : kv.second.marks) cudaEventDestroy(ev);
+    }
     h->graphs.clear();
     for (auto s : h->streams) cudaStreamDestroy(s);
     if (h->order) cudaEventDestroy(h->order);
     for (auto p : h->stf_pinned) cudaFreeHost(p);
-    if (h->dmem) cudaFree(h->dmem);
+    if (h->dmem) {
+        if (h->cfg.dev_free) h->cfg.dev_free(h->dmem, h->cfg.alloc_ctx);
+        else cudaFree(h->dmem);
+    }
     for (auto* p : h->plans) sm_plan_destroy(p);
     delete h;
     return SM_OK;

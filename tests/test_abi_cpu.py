@@ -120,3 +120,16 @@ def test_null_arguments_are_rejected(lib):
     assert lib.sm_poll(None, 1, 0, None) == -1
     assert lib.sm_close(None) == 0
     assert lib.sm_plan_destroy(None) == 0
+
+
+def test_open_rejects_an_unpaired_allocator(lib):
+    """sm_open wants dev_alloc and dev_free together (checked before any
+    device work)."""
+    from paper_1701_00581_gb300 import Channel, _lib
+    ch = (_lib.sm_channel * 1)(Channel(W=96, H=80, N=64, R=4, max_frames=4).to_c())
+    alloc = _lib.DEV_ALLOC(lambda n, ctx: None)
+    h = C.c_void_p()
+    for a, f in ((alloc, _lib.DEV_FREE()), (_lib.DEV_ALLOC(), _lib.DEV_FREE(lambda p, ctx: None))):
+        cfg = _lib.sm_config(1, ch, 1 << 20, 1, 0, 0, a, f, None)
+        assert lib.sm_open(C.byref(cfg), C.byref(h)) == _lib.SM_EINVAL
+        assert b"together" in lib.sm_last_error()

@@ -103,6 +103,52 @@ def test_ordered_bursts_finish_in_submission_order(torch):
     eng.close()
 
 
+def test_stage_times(torch):
+    """sm_result.stage_ms: every stage of the burst graph is timed; the
+    seeing stage is empty when D/r0 is given and timed when estimated; the
+    stages account for the burst's device time."""
+    from paper_1701_00581_gb300 import STAGE_NAMES, Engine
+    ch = CS.gpu_channel("ragged")
+    b = _bursts(1)[0]
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2)
+    for given in (True, False):
+        for _ in range(2):                    # first capture, then replay
+            out = np.zeros((110, 150), np.float32)
+            t = eng.submit(0, b["frames"], out, d_over_r0=b["d_over_r0"] if given else None)
+            st, res = eng.poll(t, -1)
+            assert st == 0
+            sm = res["stage_ms"]
+            assert tuple(sm) == STAGE_NAMES
+            for name in STAGE_NAMES:
+                if name == "seeing" and given:
+                    assert sm[name] == 0.0
+                else:
+                    assert sm[name] > 0.0, name
+            total = sum(sm.values())
+            assert 0.5 * res["gpu_ms"] <= total <= 1.05 * res["gpu_ms"] + 0.05
+    eng.close()
+
+
+def test_torch_allocator(torch):
+    """The engine's arena from torch's caching allocator gives the same
+    mosaic; the tensor is held while the engine is open and released by
+    close."""
+    from paper_1701_00581_gb300 import Engine
+    ch = CS.gpu_channel("ragged")
+    b = _bursts(1)[0]
+    ref_out, ref_valid = _plain(torch, ch, b)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated(0)
+    budget = 1 << 30
+    eng = Engine([ch], hbm_budget_bytes=budget, max_inflight=2, allocator="torch")
+    assert torch.cuda.memory_allocated(0) - before >= budget
+    out, valid = _serve_one(eng, b, 110, 150)
+    eng.close()
+    assert torch.cuda.memory_allocated(0) - before < budget
+    assert np.array_equal(valid, ref_valid)
+    assert np.array_equal(out, ref_out)
+
+
 def test_two_channels_in_one_engine(torch):
     from paper_1701_00581_gb300 import Channel, Engine
     c0 = CS.gpu_channel("ragged")
