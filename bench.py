@@ -45,7 +45,7 @@ METRIC = "bursts/sec and p99 latency, served vs plain, 2560x2160x100 at 1e-3 rel
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tio2560", choices=sorted(WORKLOADS))

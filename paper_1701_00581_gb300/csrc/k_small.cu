@@ -20,10 +20,13 @@ __device__ __forceinline__ float2 load_spec(const void* spec, size_t idx) {
     }
 }
 
-constexpr int STAT_THREADS = 256;
+constexpr int STAT_THREADS = 1024;
 
 // P = <|I_i|^2>, M = <I_i> over the F frames on the half box ky = 0..K;
 // noise = mean of P over {ky >= 1, |k|^2 > r^2} (the half-box corners).
+// HBM bound: one 1024-thread CTA per subfield streams its F spectra once,
+// each thread summing two neighbouring values over the frames in order
+// (16-byte loads, four frames in flight).
 template <int PREC>
 __global__ void __launch_bounds__(STAT_THREADS)
 k_stats(PlanDev p, const void* __restrict__ spec, int F, float* __restrict__ P,
@@ -38,24 +41,61 @@ k_stats(PlanDev p, const void* __restrict__ spec, int F, float* __restrict__ P,
     const float invF = 1.0f / (float)F;
     double cs = 0.0;
     int cn = 0;
-    for (int e = tid; e < ne; e += STAT_THREADS) {
-        const int ky = e / p.box_cols, col = e - ky * p.box_cols, kx = col - p.K;
-        const size_t off = (size_t)(ky + p.R) * p.box_pitch + col;
-        float ps = 0.f;
-        float2 ms = make_float2(0.f, 0.f);
-        for (int f = 0; f < F; ++f) {
-            const float2 v = load_spec<PREC>(spec, sbase + (size_t)f * box + off);
-            ps = fmaf(v.x, v.x, fmaf(v.y, v.y, ps));
-            ms.x += v.x;
-            ms.y += v.y;
+    if constexpr (PREC == SM_FP32) {
+        // two neighbouring spectrum values per thread, 16-byte loads (the
+        // pitch is a multiple of 4 and the last value of a row pairs with
+        // the row's padding, which is read but not stored)
+        const int hp = p.box_pitch / 2, ne2 = p.hb_rows * hp;
+        const float4* s4 = reinterpret_cast<const float4*>(spec);
+        for (int e = tid; e < ne2; e += STAT_THREADS) {
+            const int ky = e / hp, c2 = e - ky * hp, col = 2 * c2;
+            const size_t off = ((size_t)(ky + p.R) * p.box_pitch + col) / 2;
+            float ps0 = 0.f, ps1 = 0.f;
+            float2 m0 = make_float2(0.f, 0.f), m1 = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int f = 0; f < F; ++f) {
+                const float4 v = __ldg(s4 + (sbase + (size_t)f * box) / 2 + off);
+                ps0 = fmaf(v.x, v.x, fmaf(v.y, v.y, ps0));
+                ps1 = fmaf(v.z, v.z, fmaf(v.w, v.w, ps1));
+                m0.x += v.x; m0.y += v.y;
+                m1.x += v.z; m1.y += v.w;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cc = col + h, kx = cc - p.K;
+                if (cc >= p.box_cols) break;
+                const float pm = (h ? ps1 : ps0) * invF;
+                const float2 ms = h ? m1 : m0;
+                const size_t o = (size_t)sl * hb + (size_t)ky * p.box_pitch + cc;
+                P[o] = pm;
+                M[o] = make_float2(ms.x * invF, ms.y * invF);
+                if (ky >= 1 && kx * kx + ky * ky > p.r2i) {
+                    cs += pm;
+                    ++cn;
+                }
+            }
         }
-        const float pm = ps * invF;
-        const size_t o = (size_t)sl * hb + (size_t)ky * p.box_pitch + col;
-        P[o] = pm;
-        M[o] = make_float2(ms.x * invF, ms.y * invF);
-        if (ky >= 1 && kx * kx + ky * ky > p.r2i) {
-            cs += pm;
-            ++cn;
+    } else {
+        for (int e = tid; e < ne; e += STAT_THREADS) {
+            const int ky = e / p.box_cols, col = e - ky * p.box_cols, kx = col - p.K;
+            const size_t off = (size_t)(ky + p.R) * p.box_pitch + col;
+            float ps = 0.f;
+            float2 ms = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int f = 0; f < F; ++f) {
+                const float2 v = load_spec<PREC>(spec, sbase + (size_t)f * box + off);
+                ps = fmaf(v.x, v.x, fmaf(v.y, v.y, ps));
+                ms.x += v.x;
+                ms.y += v.y;
+            }
+            const float pm = ps * invF;
+            const size_t o = (size_t)sl * hb + (size_t)ky * p.box_pitch + col;
+            P[o] = pm;
+            M[o] = make_float2(ms.x * invF, ms.y * invF);
+            if (ky >= 1 && kx * kx + ky * ky > p.r2i) {
+                cs += pm;
+                ++cn;
+            }
         }
     }
 #pragma unroll
