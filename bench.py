@@ -116,9 +116,10 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- CPU oracle
-def oracle_sample(workload: str, frames_small=(4, 8)) -> dict:
+def oracle_samples(workload: str, frames_small=(4, 8), reps: int = 1) -> list:
     """Time the FP64 oracle, single-threaded, on one subfield at two frame counts,
-    and extrapolate linearly to a whole burst (F frames, every subfield)."""
+    and extrapolate linearly to a whole burst (F frames, every subfield).  One
+    process runs `reps` timed samples (the synthetic burst is made once)."""
     cfg, N, R = WORKLOADS[workload]
     code = f"""
 import json, os, sys, time
@@ -133,21 +134,25 @@ cubes = O.seeing_cubes(spec.W, spec.H, {N}, {N} // 2)
 s = len(subs) // 2
 c = cubes[len(cubes) // 2]
 stf = O.stf_model({N}, 0.2885, b['d_over_r0'])
-t = []
-for F in {tuple(frames_small)!r}:
-    t0 = time.perf_counter()
-    O.reconstruct_subfield(b['frames'][:F], subs[s], {N}, 0.2885, {R}, {N} // 8, stf)
-    t1 = time.perf_counter()
-    In, _, _ = O.frame_spectra(b['frames'][:F], subs[c], {N}, {N} // 8)
-    P, M = O.power_mean(In)
-    num, den = O.spectral_ratio(P, M, O.noise_floor(P, {N}, 0.2885), F, {N}, 0.2885)
-    O.fit_d_over_r0(num, den, {N}, 0.2885)
-    t.append((t1 - t0, time.perf_counter() - t1))
-print(json.dumps({{"t": t, "n_sub": len(subs), "n_cubes": len(cubes), "F": spec.F}}))
+runs = []
+for _ in range({int(reps)}):
+    t = []
+    for F in {tuple(frames_small)!r}:
+        t0 = time.perf_counter()
+        O.reconstruct_subfield(b['frames'][:F], subs[s], {N}, 0.2885, {R}, {N} // 8, stf)
+        t1 = time.perf_counter()
+        In, _, _ = O.frame_spectra(b['frames'][:F], subs[c], {N}, {N} // 8)
+        P, M = O.power_mean(In)
+        num, den = O.spectral_ratio(P, M, O.noise_floor(P, {N}, 0.2885), F, {N}, 0.2885)
+        O.fit_d_over_r0(num, den, {N}, 0.2885)
+        t.append((t1 - t0, time.perf_counter() - t1))
+    runs.append(t)
+print(json.dumps({{"runs": runs, "n_sub": len(subs), "n_cubes": len(cubes), "F": spec.F}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900 + 60 * int(reps))
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
@@ -157,14 +162,20 @@ print(json.dumps({{"t": t, "n_sub": len(subs), "n_cubes": len(cubes), "F": spec.
         per_frame = max((t2 - t1) / (f2 - f1), 0.0)
         return max(t1 - f1 * per_frame, 0.0) + d["F"] * per_frame
 
-    (a1, s1), (a2, s2) = d["t"]
-    per_burst = d["n_sub"] * extrapolate(a1, a2) + d["n_cubes"] * extrapolate(s1, s2)
-    return {"value": 1.0 / per_burst, "unit": "bursts/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 numpy oracle, 1 thread: one {N}x{N} subfield at F={f1} and F={f2} "
-                       f"({a1:.2f} s, {a2:.2f} s) and one seeing cube ({s1:.2f} s, {s2:.2f} s), "
-                       f"extrapolated linearly in F to {d['F']} frames x {d['n_sub']} subfields + "
-                       f"{d['n_cubes']} cubes = {per_burst:.0f} s per burst"),
-            "seconds": a1 + a2 + s1 + s2}
+    out = []
+    for (a1, s1), (a2, s2) in d["runs"]:
+        per_burst = d["n_sub"] * extrapolate(a1, a2) + d["n_cubes"] * extrapolate(s1, s2)
+        out.append({"value": 1.0 / per_burst, "unit": "bursts/s", "cores": 1, "kind": "oracle",
+                    "sample": (f"FP64 numpy oracle, 1 thread: one {N}x{N} subfield at F={f1} and F={f2} "
+                               f"({a1:.2f} s, {a2:.2f} s) and one seeing cube ({s1:.2f} s, {s2:.2f} s), "
+                               f"extrapolated linearly in F to {d['F']} frames x {d['n_sub']} subfields + "
+                               f"{d['n_cubes']} cubes = {per_burst:.0f} s per burst"),
+                    "seconds": a1 + a2 + s1 + s2})
+    return out
+
+
+def oracle_sample(workload: str, frames_small=(4, 8)) -> dict:
+    return oracle_samples(workload, frames_small, 1)[0]
 
 
 def run_reference(args):
@@ -172,13 +183,11 @@ def run_reference(args):
     if rank != 0:
         return
     cfg, N, _ = WORKLOADS[args.workload]
-    for _ in range(args.warmup):
-        oracle_sample(args.workload, (2, 4))
-    vals, secs = [], 0.0
-    for _ in range(args.steps):
-        s = oracle_sample(args.workload, (2, 4))
-        vals.append(s["value"])
-        secs += s["seconds"]
+    # one oracle process: W untimed samples, then K timed ones (each one
+    # subfield at F = 2 and 4 plus one seeing cube, about 5 s)
+    runs = oracle_samples(args.workload, (2, 4), args.warmup + args.steps)[args.warmup:]
+    vals = [r["value"] for r in runs]
+    s = runs[-1]
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "bursts/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
