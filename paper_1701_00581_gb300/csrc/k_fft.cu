@@ -259,12 +259,15 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
     __syncthreads();
     const float mean = reinterpret_cast<const float*>(red + WS + 1)[1];
     // remove mean * window: row transform of w_x(x) w_y(y) mu is mu w_y(y) Wx(kx)
-    for (int e = tid; e < K1 * h; e += TS) {
-        const int kx = e / h, y = e - kx * h;
-        const float a = mean * swy[y];
-        float2& c = C[kx * CP + y];
-        c.x -= a * swf[kx].x;
-        c.y -= a * swf[kx].y;
+    // (a warp per column, lanes along it: no index division per element)
+    for (int kx = warp; kx < K1; kx += WS) {
+        const float2 wf = swf[kx];
+        for (int y = lane; y < h; y += 32) {
+            const float a = mean * swy[y];
+            float2& c = C[kx * CP + y];
+            c.x -= a * wf.x;
+            c.y -= a * wf.y;
+        }
     }
     __syncthreads();
 
@@ -284,13 +287,13 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
     }
     __syncthreads();
 
-    // normalise by the windowed flux and store the box ky = -R..K
+    // normalise by the windowed flux and store the box ky = -R..K (a warp
+    // per box row, coalesced along it)
     const double fl = red[WS];
     const float inv = reinterpret_cast<const float*>(red + WS + 1)[0];
     const size_t base = ((size_t)sl * F + f) * p.box_rows * p.box_pitch;
-    const int nbox = p.box_rows * p.box_cols;
-    for (int e = tid; e < nbox; e += TS) {
-        const int row = e / p.box_cols, col = e - row * p.box_cols;
+    for (int row = warp; row < p.box_rows; row += WS)
+    for (int col = lane; col < p.box_cols; col += 32) {
         const int ky = row - p.R, kx = col - p.K;
         float2 v;
         if (kx >= 0) {
