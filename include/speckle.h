@@ -385,6 +385,15 @@ typedef struct {
                                          * mosaic                                 */
 } sm_result;
 
+/* Create an engine: one plan per channel and one device arena of
+ * hbm_budget_bytes.  With overlap_kernels = 0 (the default) the arena starts
+ * with one workspace that every burst uses in turn, sized for the largest
+ * channel's max_frames and the largest subfield chunk that leaves room for
+ * max_inflight bursts' own buffers (frames, mosaic, mask, STF table); with
+ * overlap_kernels = 1 each burst holds its own workspace in an equal share
+ * of the budget.  SM_ENOMEM when the budget cannot hold one subfield's
+ * workspace beside those buffers (shared workspace), or at submit when one
+ * burst does not fit its share.  *out is NULL on any failure.               */
 int sm_open(const sm_config* cfg, sm_handle** out);
 /* Stage one burst: copies the frames to the device (the caller may reuse
  * them on return) and queues its work.  SM_EBUSY when no slot is free.     */

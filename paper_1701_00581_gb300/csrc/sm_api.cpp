@@ -441,6 +441,7 @@ struct Job {
     float* d_out = nullptr;
     uint8_t* d_valid = nullptr;
     const double* d_seeing = nullptr;     // the burst's D / mean r0 when estimated
+    double* d_seeing_io = nullptr;        // its copy in the burst's own buffers (shared workspace)
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
     const std::vector<cudaEvent_t>* marks = nullptr;   // the burst graph's stage marks
     const std::vector<int>* mark_stage = nullptr;
@@ -482,6 +483,13 @@ struct sm_handle {
     cudaEvent_t order = nullptr;
     bool ordered = false;                 // `order` has been recorded at least once
     std::mutex launch_mu;
+    // With the bursts' kernels in submission order one workspace serves
+    // every burst (only one burst computes at a time): it sits at the start
+    // of the arena, and a burst holds only its frames, mosaic, mask, STF
+    // table and seeing value.  Concurrent kernels: one workspace per burst.
+    void* shared_ws = nullptr;
+    size_t shared_ws_bytes = 0;
+    size_t arena_bytes = 0;               // what the bursts' arena holds
 };
 
 namespace {
@@ -499,13 +507,20 @@ int log_level() {
     return lvl;
 }
 
-// Device bytes one burst of channel c holds: frames, workspace, mosaic, mask, STF.
-size_t burst_bytes(const sm_handle* h, int c, int F, sm_workspace_layout* lay) {
+// Device bytes of one burst's own buffers: frames (room for FP32), mosaic,
+// mask, STF table and the seeing value.
+size_t io_bytes(const sm_handle* h, int c, int F) {
     const sm_channel& ch = h->ch[c];
-    sm_workspace_query(h->plans[c], F, h->chunk[c], lay);
     const size_t fb = (size_t)F * ch.W * ch.H * 2;   // uint16 frames
-    return al(lay->bytes) + al(fb * 2) + al((size_t)ch.W * ch.H * 4) + al((size_t)ch.W * ch.H) +
-           al((size_t)ch.N * ch.N * sizeof(double));
+    return al(fb * 2) + al((size_t)ch.W * ch.H * 4) + al((size_t)ch.W * ch.H) +
+           al((size_t)ch.N * ch.N * sizeof(double)) + al(sizeof(double));
+}
+
+// Device bytes one burst of channel c takes from the arena: its own buffers,
+// plus its workspace unless the engine shares one.
+size_t burst_bytes(const sm_handle* h, int c, int F, sm_workspace_layout* lay) {
+    sm_workspace_query(h->plans[c], F, h->chunk[c], lay);
+    return (h->shared_ws_bytes ? 0 : al(lay->bytes)) + io_bytes(h, c, F);
 }
 
 void finish_job(sm_handle* h, Job& j) {
@@ -557,6 +572,9 @@ int launch_burst(sm_handle* h, const sm_burst* b, Job& j, const void* d_frames, 
         if (e != cudaSuccess) { drop(nullptr); return cuda_fail(e, "cudaStreamBeginCapture"); }
         rc = run_schedule(plan, calls, d_frames, b->frame_type, b->F, stf_used, ws, &lay, j.d_out, j.d_valid, st,
                           &ng.marks);
+        if (rc == SM_OK && j.d_seeing_io)
+            rc = ret(cudaMemcpyAsync(j.d_seeing_io, j.d_seeing, sizeof(double), cudaMemcpyDeviceToDevice, st),
+                     "cudaMemcpyAsync(seeing)");
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(st, &graph);
         if (rc != SM_OK) { drop(graph); return rc; }
@@ -594,18 +612,43 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
         int rc = sm_plan_create(&h->ch[c], cfg->device, &p);
         if (rc) { for (auto* q : h->plans) sm_plan_destroy(q); delete h; return rc; }
         h->plans.push_back(p);
-        // chunk: all subfields if one burst of the channel fits its share
-        // of the budget, otherwise the largest count that does
-        const size_t share = cfg->hbm_budget_bytes / (size_t)cfg->max_inflight;
+    }
+    // chunk: all subfields if the channel's workspace fits, otherwise the
+    // largest count that does.  Concurrent kernels: each burst's workspace
+    // and buffers in an equal share of the budget.  In order: one shared
+    // workspace beside max_inflight bursts' own buffers.
+    const bool shared = !cfg->overlap_kernels;
+    size_t io_max = 0;
+    for (int c = 0; c < cfg->n_channels; ++c) io_max = std::max(io_max, io_bytes(h, c, h->ch[c].max_frames));
+    const size_t io_all = io_max * (size_t)cfg->max_inflight;
+    for (int c = 0; c < cfg->n_channels; ++c) {
+        const sm_plan* p = h->plans[c];
         int lo = 1, hi = p->dev.n_sub;
         h->chunk.push_back(hi);
         sm_workspace_layout lay;
+        auto fits = [&](int chunk) {
+            h->chunk[c] = chunk;
+            if (shared) {
+                sm_workspace_query(p, h->ch[c].max_frames, chunk, &lay);
+                return io_all + al(lay.bytes) <= cfg->hbm_budget_bytes;
+            }
+            return burst_bytes(h, c, h->ch[c].max_frames, &lay) <= cfg->hbm_budget_bytes / (size_t)cfg->max_inflight;
+        };
         while (lo < hi) {
             const int mid = (lo + hi + 1) / 2;
-            h->chunk[c] = mid;
-            if (burst_bytes(h, c, h->ch[c].max_frames, &lay) <= share) lo = mid; else hi = mid - 1;
+            if (fits(mid)) lo = mid; else hi = mid - 1;
         }
         h->chunk[c] = lo;
+        if (shared) {
+            sm_workspace_query(p, h->ch[c].max_frames, lo, &lay);
+            h->shared_ws_bytes = std::max(h->shared_ws_bytes, al(lay.bytes));
+        }
+    }
+    if (shared && h->shared_ws_bytes + io_all > cfg->hbm_budget_bytes) {
+        for (auto* q : h->plans) sm_plan_destroy(q);
+        delete h;
+        set_error("hbm_budget_bytes cannot hold one subfield's workspace and the bursts' buffers");
+        return SM_ENOMEM;
     }
     cudaError_t e = cudaSuccess;
     if (cfg->dev_alloc) {
@@ -626,7 +669,9 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
         delete h;
         return cuda_fail(e, "cudaMalloc(engine arena)");
     }
-    h->arena.init(static_cast<char*>(h->dmem), cfg->hbm_budget_bytes);
+    h->arena_bytes = cfg->hbm_budget_bytes - h->shared_ws_bytes;
+    h->shared_ws = shared ? h->dmem : nullptr;
+    h->arena.init(static_cast<char*>(h->dmem) + h->shared_ws_bytes, h->arena_bytes);
     e = cudaEventCreateWithFlags(&h->order, cudaEventDisableTiming);
     if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaEventCreate"); }
     for (int i = 0; i < cfg->max_inflight; ++i) {
@@ -669,7 +714,7 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     DeviceGuard g(h->cfg.device);
     sm_workspace_layout lay;
     const size_t need = burst_bytes(h, b->channel, b->F, &lay);
-    if (need > h->cfg.hbm_budget_bytes) { set_error("burst exceeds the HBM budget"); return SM_ENOMEM; }
+    if (need > h->arena_bytes) { set_error("burst exceeds the HBM budget"); return SM_ENOMEM; }
 
     Job j;
     {
@@ -688,15 +733,23 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     }
     cudaStream_t st = h->streams[j.slot];
     char* base = h->arena.base() + j.off;
-    void* ws = base;
+    void* ws = h->shared_ws ? h->shared_ws : base;
     const size_t fbytes = (size_t)b->F * ch.W * ch.H * (b->frame_type == SM_U16 ? 2 : 4);
-    char* d_frames = base + al(lay.bytes);
+    char* d_frames = h->shared_ws ? base : base + al(lay.bytes);
     j.d_out = reinterpret_cast<float*>(d_frames + al((size_t)b->F * ch.W * ch.H * 2 * 2));
     j.d_valid = reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(j.d_out) + al((size_t)ch.W * ch.H * 4));
     double* d_stf = reinterpret_cast<double*>(reinterpret_cast<char*>(j.d_valid) + al((size_t)ch.W * ch.H));
     j.channel = b->channel;
     j.F = b->F;
-    if (est) j.d_seeing = at<double>(ws, lay.seeing) + h->plans[b->channel]->dev.n_cubes;
+    if (est) {
+        j.d_seeing = at<double>(ws, lay.seeing) + h->plans[b->channel]->dev.n_cubes;
+        if (h->shared_ws) {
+            // the next burst reuses the workspace before this one is polled:
+            // the graph copies the value into the burst's own buffers
+            j.d_seeing_io = reinterpret_cast<double*>(reinterpret_cast<char*>(d_stf) +
+                                                      al((size_t)ch.N * ch.N * sizeof(double)));
+        }
+    }
     j.host_out = b->out;
     j.host_valid = b->valid;
     cudaError_t e = cudaEventCreate(&j.ev_start);
@@ -798,7 +851,8 @@ extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result*
     cudaError_t e = cudaMemcpy(j.host_out, j.d_out, npx * sizeof(float), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && j.host_valid) e = cudaMemcpy(j.host_valid, j.d_valid, npx, cudaMemcpyDeviceToHost);
     double dr0 = 0.0;
-    if (e == cudaSuccess && j.d_seeing) e = cudaMemcpy(&dr0, j.d_seeing, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && j.d_seeing)
+        e = cudaMemcpy(&dr0, j.d_seeing_io ? j.d_seeing_io : j.d_seeing, sizeof(double), cudaMemcpyDeviceToHost);
     float gms = 0.f;
     cudaEventElapsedTime(&gms, j.ev_start, j.ev_done);
     double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};

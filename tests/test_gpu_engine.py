@@ -171,8 +171,12 @@ def test_admission_and_error_statuses(torch):
     from paper_1701_00581_gb300 import Engine, SpeckleError, _lib
     ch = CS.gpu_channel("ragged")
     b = _bursts(1)[0]
-    # a budget smaller than one burst: SM_ENOMEM
-    eng = Engine([ch], hbm_budget_bytes=1 << 20, max_inflight=1)
+    # a budget smaller than one burst: SM_ENOMEM, from sm_open for the shared
+    # workspace, from sm_submit_burst for per-burst workspaces
+    with pytest.raises(SpeckleError) as e:
+        Engine([ch], hbm_budget_bytes=1 << 20, max_inflight=1)
+    assert e.value.status == _lib.SM_ENOMEM
+    eng = Engine([ch], hbm_budget_bytes=1 << 20, max_inflight=1, overlap_kernels=True)
     with pytest.raises(SpeckleError) as e:
         eng.submit(0, b["frames"], np.zeros((110, 150), np.float32), d_over_r0=b["d_over_r0"])
     assert e.value.status == _lib.SM_ENOMEM
