@@ -85,6 +85,43 @@ def test_alone_equals_in_the_mix(torch, overlap):
         assert np.array_equal(o, m)
 
 
+def test_two_host_threads_share_an_engine(torch):
+    """Submit and poll from two host threads at once (the handle is locked
+    internally): every burst's mosaic equals the same burst served alone."""
+    import threading
+    import time
+    from paper_1701_00581_gb300 import Engine
+    ch = CS.gpu_channel("ragged")
+    bursts = _bursts(6)
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2)
+    alone = [_serve_one(eng, b, 110, 150)[0] for b in bursts]
+    outs = [np.zeros((110, 150), np.float32) for _ in bursts]
+    errors = []
+
+    def worker(idx):
+        try:
+            for i in idx:
+                t = None
+                while t is None:
+                    t = eng.try_submit(0, bursts[i]["frames"], outs[i], d_over_r0=bursts[i]["d_over_r0"])
+                    if t is None:
+                        time.sleep(0.001)
+                st, _ = eng.poll(t, -1)
+                assert st == 0
+        except Exception as e:          # reported by the main thread
+            errors.append(e)
+
+    th = [threading.Thread(target=worker, args=(range(k, len(bursts), 2),)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=120)
+    eng.close()
+    assert not errors, errors
+    for a, o in zip(alone, outs):
+        assert np.array_equal(a, o)
+
+
 def test_ordered_bursts_finish_in_submission_order(torch):
     """With overlap_kernels off, a burst's kernels start after the previous
     burst's have finished: once the last ticket is done, every earlier one
