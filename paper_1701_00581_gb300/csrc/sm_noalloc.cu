@@ -12,11 +12,12 @@
 
 using namespace smi;
 
-namespace {
-
 // Fixed scratch workspace.  Every GPU that loads this library holds these
-// bytes until the process exits.
-__device__ __align__(256) unsigned char g_noalloc_scratch[SM_NOALLOC_SCRATCH_BYTES];
+// bytes until the process exits.  In host code the name is only a handle for
+// cudaGetSymbolAddress, never a device pointer.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
