@@ -116,61 +116,96 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- CPU oracle
+def _oracle_subfield_task(task):
+    """One host core's share of the CPU baseline: the FP64 oracle on one
+    subfield at two frame counts and on one seeing cube at the same counts
+    (seconds for each).  Runs in a spawned worker with one BLAS thread."""
+    import time as _t
+    from oracle import speckle_oracle as O
+    path, sub, cube, N, R, frames_small, d_over_r0 = task
+    frames = np.load(path, mmap_mode="r")
+    stf = O.stf_model(N, 0.2885, d_over_r0)
+    out = []
+    for F in frames_small:
+        fr = np.asarray(frames[:F])
+        t0 = _t.perf_counter()
+        O.reconstruct_subfield(fr, sub, N, 0.2885, R, N // 8, stf)
+        t1 = _t.perf_counter()
+        In, _, _ = O.frame_spectra(fr, cube, N, N // 8)
+        P, M = O.power_mean(In)
+        num, den = O.spectral_ratio(P, M, O.noise_floor(P, N, 0.2885), F, N, 0.2885)
+        O.fit_d_over_r0(num, den, N, 0.2885)
+        out.append((t1 - t0, _t.perf_counter() - t1))
+    return out
+
+
 def oracle_samples(workload: str, frames_small=(4, 8), reps: int = 1) -> list:
-    """Time the FP64 oracle, single-threaded, on one subfield at two frame counts,
-    and extrapolate linearly to a whole burst (F frames, every subfield).  One
-    process runs `reps` timed samples (the synthetic burst is made once)."""
+    """Time the FP64 oracle on all host cores (os.sched_getaffinity): a pool of
+    one spawned worker per core, each reconstructing its own subfield (and
+    fitting one seeing cube) at two frame counts, all at once; the per-core
+    times are extrapolated linearly in F to the workload's frame count and
+    over ceil(n_sub / cores) rounds of subfields plus ceil(n_cubes / cores)
+    rounds of cubes.  One process runs `reps` timed samples (the synthetic
+    burst is made once)."""
     cfg, N, R = WORKLOADS[workload]
     code = f"""
-import json, os, sys, time
+import json, math, multiprocessing as mp, os, sys, tempfile, time
 sys.path.insert(0, {ROOT!r})
 import numpy as np
 from synth import CONFIGS, make_burst
 from oracle import speckle_oracle as O
+from bench import _oracle_subfield_task
 spec = CONFIGS[{cfg!r}]
 b = make_burst(spec, F={max(frames_small)}, burst=99)
 subs = O.subfield_grid(spec.W, spec.H, {N}, {N} // 2)
 cubes = O.seeing_cubes(spec.W, spec.H, {N}, {N} // 2)
-s = len(subs) // 2
-c = cubes[len(cubes) // 2]
-stf = O.stf_model({N}, 0.2885, b['d_over_r0'])
+cores = len(os.sched_getaffinity(0))
 runs = []
-for _ in range({int(reps)}):
-    t = []
-    for F in {tuple(frames_small)!r}:
-        t0 = time.perf_counter()
-        O.reconstruct_subfield(b['frames'][:F], subs[s], {N}, 0.2885, {R}, {N} // 8, stf)
-        t1 = time.perf_counter()
-        In, _, _ = O.frame_spectra(b['frames'][:F], subs[c], {N}, {N} // 8)
-        P, M = O.power_mean(In)
-        num, den = O.spectral_ratio(P, M, O.noise_floor(P, {N}, 0.2885), F, {N}, 0.2885)
-        O.fit_d_over_r0(num, den, {N}, 0.2885)
-        t.append((t1 - t0, time.perf_counter() - t1))
-    runs.append(t)
-print(json.dumps({{"runs": runs, "n_sub": len(subs), "n_cubes": len(cubes), "F": spec.F}}))
+with tempfile.TemporaryDirectory() as tmp:
+    path = os.path.join(tmp, "frames.npy")
+    np.save(path, b["frames"])
+    tasks = [(path, subs[(len(subs) // 2 + 7 * k) % len(subs)], subs[cubes[(len(cubes) // 2 + k) % len(cubes)]],
+              {N}, {R}, {tuple(frames_small)!r}, b["d_over_r0"]) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for _ in range({int(reps)}):
+            t0 = time.perf_counter()
+            per = pool.map(_oracle_subfield_task, tasks, chunksize=1)
+            wall = time.perf_counter() - t0
+            runs.append({{"per": per, "wall": wall}})
+print(json.dumps({{"runs": runs, "n_sub": len(subs), "n_cubes": len(cubes), "F": spec.F, "cores": cores}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT,
                        timeout=900 + 60 * int(reps))
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
     (f1, f2) = frames_small
+    cores = d["cores"]
 
     def extrapolate(t1, t2):           # linear in F, to the workload's F
         per_frame = max((t2 - t1) / (f2 - f1), 0.0)
         return max(t1 - f1 * per_frame, 0.0) + d["F"] * per_frame
 
     out = []
-    for (a1, s1), (a2, s2) in d["runs"]:
-        per_burst = d["n_sub"] * extrapolate(a1, a2) + d["n_cubes"] * extrapolate(s1, s2)
-        out.append({"value": 1.0 / per_burst, "unit": "bursts/s", "cores": 1, "kind": "oracle",
-                    "sample": (f"FP64 numpy oracle, 1 thread: one {N}x{N} subfield at F={f1} and F={f2} "
-                               f"({a1:.2f} s, {a2:.2f} s) and one seeing cube ({s1:.2f} s, {s2:.2f} s), "
-                               f"extrapolated linearly in F to {d['F']} frames x {d['n_sub']} subfields + "
-                               f"{d['n_cubes']} cubes = {per_burst:.0f} s per burst"),
-                    "seconds": a1 + a2 + s1 + s2})
+    for run in d["runs"]:
+        per = run["per"]                # per core: [(sub, cube) at f1, (sub, cube) at f2]
+        a1 = statistics.mean(p[0][0] for p in per)
+        a2 = statistics.mean(p[1][0] for p in per)
+        s1 = statistics.mean(p[0][1] for p in per)
+        s2 = statistics.mean(p[1][1] for p in per)
+        rounds_sub = -(-d["n_sub"] // cores)
+        rounds_cube = -(-d["n_cubes"] // cores)
+        per_burst = rounds_sub * extrapolate(a1, a2) + rounds_cube * extrapolate(s1, s2)
+        out.append({"value": 1.0 / per_burst, "unit": "bursts/s", "cores": cores, "kind": "oracle",
+                    "sample": (f"FP64 numpy oracle on {cores} host cores (one spawned worker per core, one BLAS "
+                               f"thread each): {cores} {N}x{N} subfields at once at F={f1} and F={f2} "
+                               f"(mean {a1:.2f} s, {a2:.2f} s per subfield) and {cores} seeing cubes "
+                               f"({s1:.2f} s, {s2:.2f} s), extrapolated linearly in F to {d['F']} frames and "
+                               f"over {rounds_sub} rounds of subfields ({d['n_sub']}) + {rounds_cube} of cubes "
+                               f"({d['n_cubes']}) = {per_burst:.0f} s per burst"),
+                    "seconds": run["wall"]})
     return out
 
 
@@ -184,7 +219,8 @@ def run_reference(args):
         return
     cfg, N, _ = WORKLOADS[args.workload]
     # one oracle process: W untimed samples, then K timed ones (each one
-    # subfield at F = 2 and 4 plus one seeing cube, about 5 s)
+    # subfield per host core at F = 2 and 4 plus one seeing cube per core,
+    # about 5 s)
     runs = oracle_samples(args.workload, (2, 4), args.warmup + args.steps)[args.warmup:]
     vals = [r["value"] for r in runs]
     s = runs[-1]
@@ -193,7 +229,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"{args.workload} burst (FP64 oracle sample)"},
-            "cpu_baseline": {"value": v, "unit": "bursts/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "bursts/s", "cores": s["cores"], "kind": "oracle",
                              "sample": s["sample"]},
             "e2e": {"value": v, "unit": "bursts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -301,7 +301,8 @@ int sm_reconstruct(const sm_plan* plan, const void* frames, int frame_type, int 
  * are running, such as a camera or telescope control loop that fixes all of
  * its device memory at start-up (an allocation can synchronise the device
  * and stall frame acquisition), or a plug-in whose host framework owns every
- * device allocation.  Same arguments and result as sm_reconstruct, but the
+ * device allocation.  Same arguments and result as sm_reconstruct (stf may
+ * be NULL: the seeing is then estimated from the burst, Sect. 3.1), but the
  * workspace is a fixed array of SM_NOALLOC_SCRATCH_BYTES in the library's
  * own device image (every GPU that loads the library holds it until the
  * process exits), so the call allocates nothing.  Subfields go through in
@@ -385,7 +386,18 @@ typedef struct {
                                          * mosaic                                 */
 } sm_result;
 
-/* Create an engine: one plan per channel and one device arena of
+/* The serving calls restate the paper's statement of the problem for a
+ * stream of bursts: a burst of F >= 100 short exposures of one channel
+ * (Sect. 2, Table 1: H-alpha 1024 x 1024, TiO and G-band 2560 x 2160, each at
+ * 10 frames/s) goes in, and one reconstructed mosaic comes out, computed
+ * subfield by subfield and merged (Sect. 2, Sect. 3.2), with the seeing
+ * estimated from the burst itself (Sect. 3.1) unless given.  The paper runs
+ * one burst at a time on an MPI cluster; admission of bursts by a device
+ * memory budget, tickets, overlap of one burst's copies with another's
+ * kernels and the latency record are this library's serving design, not the
+ * paper's.
+ *
+ * sm_open: create an engine: one plan per channel and one device arena of
  * hbm_budget_bytes.  With overlap_kernels = 0 (the default) the arena starts
  * with one workspace that every burst uses in turn, sized for the largest
  * channel's max_frames and the largest subfield chunk that leaves room for
@@ -395,15 +407,31 @@ typedef struct {
  * workspace beside those buffers (shared workspace), or at submit when one
  * burst does not fit its share.  *out is NULL on any failure.               */
 int sm_open(const sm_config* cfg, sm_handle** out);
-/* Stage one burst: copies the frames to the device (the caller may reuse
- * them on return) and queues its work.  SM_EBUSY when no slot is free.     */
+/* sm_submit_burst: stage one burst (Sect. 2: the frames of one burst of one
+ * channel) -- copies the frames to the device (the caller may reuse them on
+ * return) and queues its whole reconstruction (Sect. 2, 3.1, 3.2).  The
+ * returned ticket names the burst for sm_poll.  SM_EBUSY when no slot or no
+ * budget is free now (retry after a poll), SM_ENOMEM when the burst can never
+ * fit the budget, SM_EINVAL for a bad burst.  With the environment variable
+ * SM_FAULT=alloc:N set when the engine is opened, the N-th admission of that
+ * engine (counting from 1) fails as if its arena allocation had failed: the
+ * burst gets a ticket, nothing is queued, and sm_poll reports SM_ENOMEM for
+ * it; the engine stays usable (a host-side failure injection for tests).   */
 int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket);
-/* Wait up to timeout_ms (0 = test, <0 = forever).  SM_OK once the mosaic
- * has been copied into b->out; then the ticket is released.               */
+/* sm_poll: the mosaic of one burst (Sect. 3.2: the merged image) -- wait
+ * up to timeout_ms (0 = test and return SM_PENDING, > 0 = return SM_ETIMEDOUT
+ * when it elapses, < 0 = forever).  SM_OK once the mosaic (and mask) have been
+ * copied into the burst's out (and valid) buffers; res gets the latency
+ * record and per-stage device times; then the ticket is released.  A ticket
+ * whose work failed reports that status once and is released.              */
 int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result* res);
-/* Cancel pending tickets, wait for the device, free everything.           */
+/* sm_close: end the engine -- cancel pending tickets, wait for the device,
+ * free everything.  (The paper's master process ends after the mosaic is
+ * written, Sect. 3.2; here the engine outlives any number of bursts.)      */
 int sm_close(sm_handle* h);
 
+/* sm_strerror: text of a status code of this library (no paper
+ * counterpart).                                                             */
 const char* sm_strerror(int status);
 /* Last CUDA or validation message of this thread (never NULL). */
 const char* sm_last_error(void);

@@ -490,6 +490,10 @@ struct sm_handle {
     void* shared_ws = nullptr;
     size_t shared_ws_bytes = 0;
     size_t arena_bytes = 0;               // what the bursts' arena holds
+    // Host-side failure injection (SM_FAULT=alloc:N at sm_open): admission
+    // number fault_alloc_at (from 1) fails as if its arena allocation had.
+    long long fault_alloc_at = 0;
+    long long n_admitted = 0;
 };
 
 namespace {
@@ -603,6 +607,10 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
     sm_handle* h = new (std::nothrow) sm_handle();
     if (!h) { set_error("host allocation failed"); return SM_ENOMEM; }
     h->cfg = *cfg;
+    if (const char* f = getenv("SM_FAULT")) {
+        long long n = 0;
+        if (sscanf(f, "alloc:%lld", &n) == 1 && n > 0) h->fault_alloc_at = n;
+    }
     h->ch.assign(cfg->ch, cfg->ch + cfg->n_channels);
     h->cfg.ch = h->ch.data();
     h->t0 = Clock::now();
@@ -719,6 +727,18 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     Job j;
     {
         std::lock_guard<std::mutex> lk(h->mu);
+        if (h->fault_alloc_at > 0 && ++h->n_admitted == h->fault_alloc_at) {
+            // injected allocation failure: the burst gets a ticket that
+            // reports SM_ENOMEM, nothing is queued, no slot or budget is held
+            j.ticket = h->next_ticket++;
+            j.channel = b->channel;
+            j.F = b->F;
+            j.status = SM_ENOMEM;
+            j.t_submit = ms_since(h->t0);
+            *ticket = j.ticket;
+            h->jobs[j.ticket] = j;
+            return SM_OK;
+        }
         int slot = -1;
         for (size_t i = 0; i < h->streams.size(); ++i)
             if (!h->stream_busy[i]) { slot = (int)i; break; }
@@ -819,6 +839,20 @@ extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result*
             std::lock_guard<std::mutex> lk(h->mu);
             auto it = h->jobs.find(ticket);
             if (it == h->jobs.end()) { set_error("unknown ticket"); return SM_ENOTFOUND; }
+            if (it->second.status < 0) {
+                // a burst that failed before it was queued reports once
+                const int rc = it->second.status;
+                set_error(rc == SM_ENOMEM ? "burst allocation failed (injected by SM_FAULT)" : "burst failed");
+                if (res) {
+                    std::memset(res, 0, sizeof(*res));
+                    res->status = rc;
+                    res->t_submit_ms = it->second.t_submit;
+                    res->t_done_ms = ms_since(h->t0);
+                }
+                finish_job(h, it->second);
+                h->jobs.erase(it);
+                return rc;
+            }
             ev = it->second.ev_done;
         }
         DeviceGuard g(h->cfg.device);

@@ -27,7 +27,7 @@ void* g_addr[kMaxDevices] = {};
 
 extern "C" int sm_reconstruct_noalloc(const sm_plan* plan, const void* frames, int frame_type, int F,
                                       const double* stf, float* out, uint8_t* valid, void* stream) {
-    if (!plan || !frames || !stf || !out) { set_error("NULL plan, frames, stf or out"); return SM_EINVAL; }
+    if (!plan || !frames || !out) { set_error("NULL plan, frames or out"); return SM_EINVAL; }
     if (F < 1 || F > plan->ch.max_frames) { set_error("F out of range 1..max_frames"); return SM_EINVAL; }
     if (plan->device < 0 || plan->device >= kMaxDevices) { set_error("device index too large"); return SM_EINVAL; }
     // the largest chunk of subfields whose workspace fits the fixed scratch

@@ -255,3 +255,78 @@ def test_close_with_pending_tickets(torch):
     o, _ = _serve_one(eng2, bursts[0], 110, 150)
     eng2.close()
     assert np.isfinite(o).all()
+
+
+def test_served_burst_with_estimated_seeing_matches_the_oracle(torch):
+    """The path the served end-to-end number times, checked against the oracle
+    directly: frames from host memory, no STF and no D/r0 (the engine
+    estimates the seeing from the burst, Sect. 3.1), mosaic copied back to
+    the host; image rel L2 1e-3 and the valid mask exact."""
+    from oracle import speckle_oracle as O
+    from paper_1701_00581_gb300 import Engine
+    c = CS.RAGGED
+    ch = CS.gpu_channel("ragged")
+    b = _bursts(1)[0]
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2)
+    out = np.zeros((110, 150), np.float32)
+    valid = np.zeros((110, 150), np.uint8)
+    t = eng.submit(0, b["frames"], out, valid)
+    st, res = eng.poll(t, -1)
+    eng.close()
+    assert st == 0 and res["d_over_r0"] > 0
+    ref = O.reconstruct_burst(b["frames"], c["N"], c["stride"], CS.FC, c["R"], c["taper"], None)
+    _, x_burst = O.estimate_seeing(b["frames"], c["N"], c["stride"], CS.FC, c["taper"])
+    assert abs(res["d_over_r0"] - x_burst) < 2e-3 * x_burst
+    v = ref["valid"]
+    assert np.array_equal(valid.astype(bool), v)
+    assert CS.rel_l2(out[v], ref["out"][v]) < 1e-3
+    assert np.all(out[~v] == 0)
+
+
+def test_poll_with_a_positive_timeout_times_out_then_completes(torch):
+    """sm_poll with timeout_ms > 0 on a burst that needs longer returns
+    SM_ETIMEDOUT (the ticket stays valid) and later SM_OK."""
+    from paper_1701_00581_gb300 import Channel, Engine, _lib
+    spec = S.BurstSpec(W=1024, H=1024, F=40, N=128, dr0=(5.0, 12.0), counts=True)
+    b = S.make_burst(spec, channel=12, burst=0)
+    ch = Channel(W=1024, H=1024, N=128, R=16, max_frames=40)
+    eng = Engine([ch], hbm_budget_bytes=16 << 30, max_inflight=1)
+    out = np.zeros((1024, 1024), np.float32)
+    # the first burst captures its graph; the timed one replays it
+    t = eng.submit(0, b["frames"], out)
+    assert eng.poll(t, -1)[0] == _lib.SM_OK
+    t = eng.submit(0, b["frames"], out)
+    st, res = eng.poll(t, 1)
+    assert st == _lib.SM_ETIMEDOUT and res is None
+    st, res = eng.poll(t, -1)
+    assert st == _lib.SM_OK and res["gpu_ms"] > 1.0
+    eng.close()
+
+
+def test_injected_allocation_failure_reports_on_its_ticket(torch, monkeypatch):
+    """SM_FAULT=alloc:2: the second admission fails as if its arena allocation
+    had; its ticket reports SM_ENOMEM once, the others are served, and the
+    engine stays usable (a host-side injection: no GPU fault)."""
+    from paper_1701_00581_gb300 import Engine, SpeckleError, _lib
+    ch = CS.gpu_channel("ragged")
+    bursts = _bursts(3)
+    monkeypatch.setenv("SM_FAULT", "alloc:2")
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2)
+    monkeypatch.delenv("SM_FAULT")
+    outs = [np.zeros((110, 150), np.float32) for _ in bursts]
+    tickets = [eng.submit(0, b["frames"], o, d_over_r0=b["d_over_r0"]) for b, o in zip(bursts[:2], outs[:2])]
+    with pytest.raises(SpeckleError) as e:
+        eng.poll(tickets[1], -1)
+    assert e.value.status == _lib.SM_ENOMEM
+    with pytest.raises(SpeckleError) as e:           # reported once, then released
+        eng.poll(tickets[1], 0)
+    assert e.value.status == _lib.SM_ENOTFOUND
+    assert eng.poll(tickets[0], -1)[0] == _lib.SM_OK
+    # the failed burst held no slot: the engine takes two more
+    t2 = eng.submit(0, bursts[2]["frames"], outs[2], d_over_r0=bursts[2]["d_over_r0"])
+    t1 = eng.submit(0, bursts[1]["frames"], outs[1], d_over_r0=bursts[1]["d_over_r0"])
+    assert eng.poll(t2, -1)[0] == _lib.SM_OK and eng.poll(t1, -1)[0] == _lib.SM_OK
+    eng.close()
+    for b, o in zip(bursts, outs):
+        ref, _ = _plain(torch, ch, b)
+        assert np.array_equal(o, ref)

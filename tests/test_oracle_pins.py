@@ -309,14 +309,89 @@ def test_recursion_exact_for_single_noise_free_frame(weight):
     assert np.max(np.abs(zi[U[:, 1] + c, U[:, 0] + c] - exp)) < 1e-10
 
 
+# Splits of the recursion on 8 x 8 at r^2 = 5, R = 2, worked out by hand:
+# w = (1, 1): v = (1, 0), (0, 1) [u = (0, 1), (1, 0)]; w = (-1, 1): mirror in x;
+# w = (2, 0): v = (1, 0), (1, 1), (1, -1) [u = (1, 0), (1, -1), (1, 1)]; w = (0, 2):
+# v = (0, 1), (1, 1), (-1, 1); w = (2, 1): v = (1, 0), (0, 1), (1, 1), (2, 0)
+# [|u|^2 = 2, 4, 1, 1; v = (1, -1) gives |u|^2 = 5, not below |w|^2]; (1, 2) and
+# (-1, 2), (-2, 1) by the x <-> y swap and the mirrors.
+SPLITS_8X8_R2 = {
+    (1, 1): {(1, 0), (0, 1)},
+    (-1, 1): {(-1, 0), (0, 1)},
+    (2, 0): {(1, 0), (1, 1), (1, -1)},
+    (0, 2): {(0, 1), (1, 1), (-1, 1)},
+    (2, 1): {(1, 0), (0, 1), (1, 1), (2, 0)},
+    (1, 2): {(0, 1), (1, 0), (1, 1), (0, 2)},
+    (-1, 2): {(0, 1), (-1, 0), (-1, 1), (0, 2)},
+    (-2, 1): {(-1, 0), (0, 1), (-1, 1), (-2, 0)},
+}
+
+
+def _splits_bruteforce(N, fc, R):
+    """Every (w, v) of the recursion from the definition, by exhaustive search
+    over the integer box: w in the upper half plane, 2 <= |w|^2 <= r^2,
+    0 < |v|^2 <= R^2, |v|^2 < |w|^2 and |w - v|^2 < |w|^2."""
+    r2 = (fc * N) ** 2
+    out = set()
+    for wy in range(0, N // 2):
+        for wx in range(-N // 2, N // 2):
+            w2 = wx * wx + wy * wy
+            if not (wy > 0 or (wy == 0 and wx > 0)) or w2 < 2 or w2 > r2:
+                continue
+            for vy in range(-R, R + 1):
+                for vx in range(-R, R + 1):
+                    v2 = vx * vx + vy * vy
+                    u2 = (wx - vx) ** 2 + (wy - vy) ** 2
+                    if 0 < v2 <= R * R and v2 < w2 and u2 < w2:
+                        out.add((wx, wy, vx, vy))
+    return out
+
+
+def test_recursion_splits_hand_worked_8x8():
+    """The split list on 8 x 8 (r^2 = 5), R = 2, against the hand-worked table:
+    8 recursion points, 26 splits."""
+    sp = O.recursion_splits(8, math.sqrt(5) / 8, 2)
+    got = {}
+    for wx, wy, vx, vy in sp.tolist():
+        got.setdefault((wx, wy), set()).add((vx, vy))
+    assert len(sp) == 26 and len({tuple(x) for x in sp.tolist()}) == 26
+    assert got == SPLITS_8X8_R2
+
+
+@pytest.mark.parametrize("N,R", [(16, 3), (32, 4), (64, 8)])
+def test_recursion_splits_match_exhaustive_search(N, R):
+    sp = O.recursion_splits(N, FC, R)
+    assert {tuple(x) for x in sp.tolist()} == _splits_bruteforce(N, FC, R)
+    assert len({tuple(x) for x in sp.tolist()}) == len(sp)
+
+
+def test_recursion_reads_exactly_the_splits():
+    """phase_recursion's own split condition agrees with recursion_splits: a
+    bispectrum that is 1 on the listed splits and NaN elsewhere recovers unit
+    phasors without touching a NaN."""
+    N, R = 16, 3
+    pairs = O.pair_domain(N, FC, R)
+    listed = set()
+    for wx, wy, vx, vy in O.recursion_splits(N, FC, R).tolist():
+        ux, uy = wx - vx, wy - vy
+        listed.add((ux, uy, vx, vy) if (uy > 0 or (uy == 0 and ux > 0)) else (-ux, -uy, -vx, -vy))
+    B = np.array([1.0 + 0j if tuple(p) in listed else np.nan for p in pairs.tolist()])
+    M = np.ones((N, N), dtype=np.complex128)
+    z = O.phase_recursion(B, pairs, M, N, FC, R)
+    U = O.domain_U(N, FC)
+    vals = z[U[:, 1] + N // 2, U[:, 0] + N // 2]
+    assert np.all(np.isfinite(vals)) and np.allclose(vals, 1.0)
+
+
 def _split_objective(z, B, pairs, N, R, weight, P):
     """J(z) = sum over the recursion's splits of g Re[conj B(u,v) z(u) z(v) conj z(w)],
-    written out pair by pair (lower-half u looked up as conj B(-u, -v))."""
+    written out pair by pair (lower-half u looked up as conj B(-u, -v)); the
+    splits come from the exhaustive search, not from the oracle."""
     K = int(math.floor(O.cutoff_radius(N, FC)))
     lookup = {tuple(p): i for i, p in enumerate(pairs.tolist())}
     c = N // 2
     J = 0.0
-    for wx, wy, vx, vy in O.recursion_splits(N, FC, R).tolist():
+    for wx, wy, vx, vy in sorted(_splits_bruteforce(N, FC, R)):
         ux, uy = wx - vx, wy - vy
         if uy > 0 or (uy == 0 and ux > 0):
             b = B[lookup[(ux, uy, vx, vy)]]

@@ -1,20 +1,26 @@
 """The allocation-free whole-path entry point, sm_reconstruct_noalloc.
 
-Callers that may not allocate device memory while they run (a camera loop
-that fixes its device memory at start-up, a plug-in whose host framework
-owns every allocation) call this entry point instead of sm_reconstruct; it
-works on a fixed scratch array inside the library.  Its mosaic must match
-the one sm_reconstruct computes on a caller-provided workspace, call after
-call.  This file is collected last on purpose.
+Some callers may not allocate device memory once they are running: a camera
+or telescope control loop that fixes its device memory at start-up (an
+allocation can synchronise the device and stall frame acquisition), or a
+plug-in whose host framework owns every device allocation.  They call this
+entry point instead of sm_reconstruct; it works on a fixed scratch array
+inside the library.  It runs the same kernels in the same order as
+sm_reconstruct does with the same subfield chunk, so its mosaic must equal
+that one bit for bit, call after call, whether the whole burst fits the
+array at once, goes through it in chunks, or has its seeing estimated from
+the burst.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
+
+from synth import burst as S
 
 from . import _cases as CS
 
 pytestmark = pytest.mark.gpu
 
-IMG_TOL = 1e-3
+SCRATCH_BYTES = 64 << 20          # SM_NOALLOC_SCRATCH_BYTES of speckle.h
 
 
 @pytest.fixture(scope="module")
@@ -27,29 +33,73 @@ def torch():
     return t
 
 
-def test_noalloc_matches_workspace_entry_on_two_calls(torch):
+def _largest_chunk(plan, F):
+    """The chunk the entry point picks: the most subfields whose workspace fits."""
+    best = 0
+    for n in range(1, plan.info["n_sub"] + 1):
+        if plan.layout(F, n).bytes <= SCRATCH_BYTES:
+            best = n
+        else:
+            break
+    return best
+
+
+def _compare(torch, plan, frames_np, stf_np, calls=2):
+    F, (H, W) = frames_np.shape[0], frames_np.shape[1:]
+    dev = "cuda:0"
+    frames = torch.from_numpy(frames_np).to(dev)
+    stf = None if stf_np is None else torch.from_numpy(stf_np).to(dev)
+    chunk = _largest_chunk(plan, F)
+    assert chunk >= 1
+    ws, lay = plan.workspace(F, chunk)
+    ref = torch.zeros((H, W), device=dev)
+    ref_valid = torch.zeros((H, W), dtype=torch.uint8, device=dev)
+    plan.reconstruct(frames, F, stf, chunk, ws, lay, ref, ref_valid)
+    torch.cuda.synchronize()
+    ref_np, v = ref.cpu().numpy(), ref_valid.cpu().numpy()
+    del ws
+    for _ in range(calls):
+        out = torch.full((H, W), -1.0, device=dev)
+        valid = torch.full((H, W), 7, dtype=torch.uint8, device=dev)
+        plan.reconstruct_noalloc(frames, F, stf, out, valid)
+        torch.cuda.synchronize()
+        assert np.array_equal(valid.cpu().numpy(), v)
+        assert np.array_equal(out.cpu().numpy(), ref_np)
+    return chunk, ref_np, v.astype(bool)
+
+
+def test_noalloc_equals_workspace_entry_on_two_calls(torch):
     from paper_1701_00581_gb300 import Plan
     plan = Plan(CS.gpu_channel("ragged"))
     b = CS.burst("ragged")
-    F, n = b["frames"].shape[0], plan.info["n_sub"]
-    dev = "cuda:0"
-    frames = torch.from_numpy(b["frames"]).to(dev)
-    stf = torch.from_numpy(b["stf_emp"]).to(dev)
-    ws, lay = plan.workspace(F, n)
-    ref = torch.zeros((110, 150), device=dev)
-    ref_valid = torch.zeros((110, 150), dtype=torch.uint8, device=dev)
-    plan.reconstruct(frames, F, stf, n, ws, lay, ref, ref_valid)
-    torch.cuda.synchronize()
-    ref_np, v = ref.cpu().numpy(), ref_valid.cpu().numpy().astype(bool)
-    for _ in range(2):
-        out = torch.full((110, 150), -1.0, device=dev)
-        valid = torch.zeros((110, 150), dtype=torch.uint8, device=dev)
-        plan.reconstruct_noalloc(frames, F, stf, out, valid)
-        torch.cuda.synchronize()
-        got = out.cpu().numpy()
-        assert np.array_equal(valid.cpu().numpy().astype(bool), v)
-        assert CS.rel_l2(got[v], ref_np[v]) < IMG_TOL
-        assert np.all(got[~v] == 0)
+    chunk, out, v = _compare(torch, plan, b["frames"], b["stf_emp"])
+    assert chunk == plan.info["n_sub"]                # the whole burst fits at once
+    o = CS.oracle_run("ragged")
+    assert np.array_equal(v, o["valid"])
+    assert CS.rel_l2(out[v], o["out"][v]) < 1e-3
+
+
+def test_noalloc_estimates_the_seeing_without_an_stf(torch):
+    from paper_1701_00581_gb300 import Plan
+    plan = Plan(CS.gpu_channel("ragged"))
+    b = CS.burst("ragged")
+    _compare(torch, plan, b["frames"], None)
+
+
+def test_noalloc_chunks_a_burst_larger_than_the_scratch(torch):
+    """A 1024 x 1024 channel (225 subfields of 128^2, |v| <= 16): its whole
+    workspace exceeds the array, one subfield fits, so the burst goes through
+    in chunks -- with the STF given and with the seeing estimated (the
+    two-pass schedule)."""
+    from paper_1701_00581_gb300 import Channel, Plan
+    spec = S.BurstSpec(W=1024, H=1024, F=4, N=128, dr0=(5.0, 12.0), counts=True)
+    b = S.make_burst(spec, channel=13, burst=0)
+    plan = Plan(Channel(W=1024, H=1024, N=128, R=16, max_frames=4))
+    assert plan.layout(4, plan.info["n_sub"]).bytes > SCRATCH_BYTES
+    stf = plan.model_stf(b["d_over_r0"])
+    chunk, _, _ = _compare(torch, plan, b["frames"], stf, calls=1)
+    assert 1 <= chunk < plan.info["n_sub"]
+    _compare(torch, plan, b["frames"], None, calls=2)
 
 
 def test_noalloc_rejects_a_channel_too_large_for_the_scratch(torch):
