@@ -40,6 +40,7 @@ WORKLOADS = {
 FP32_LANES_PER_SM = 128
 FLOPS_PER_TRIPLE = 14          # two complex products + one complex add
 METRIC = "bursts/sec and p99 latency, served vs plain, 2560x2160x100 at 1e-3 rel L2"
+MODE_NAMES = {0: "submission", 1: "concurrent", 2: "pipelined"}
 
 
 def parse():
@@ -59,8 +60,11 @@ def parse():
     ap.add_argument("--weight", default="bispec", choices=["bispec", "unit", "snr"], help="phase-term weighting")
     ap.add_argument("--iters", type=int, default=0, help="least-squares phase sweeps after the recursion")
     ap.add_argument("--inflight", type=int, default=2, help="bursts in flight on the served e2e path")
-    ap.add_argument("--overlap", action="store_true",
-                    help="served paths: run admitted bursts' kernels concurrently instead of in submission order")
+    ap.add_argument("--batch", type=int, default=4,
+                    help="bursts per batched persistent launch in the batched record (0: skip it)")
+    ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2],
+                    help="served paths: 0 bursts' kernels in submission order, 1 concurrently, 2 pipelined (a "
+                         "burst's phase/inverse/mosaic beside the next burst's transforms and bispectrum)")
     ap.add_argument("--layout", default="overlap50", choices=["overlap50", "paper"],
                     help="overlap50: stride N/2, ragged edges padded, blended mosaic; paper: stride N/4, "
                          "full tiles only, central-block mosaic (1110 cubes, 2368x1920 for TiO)")
@@ -253,7 +257,7 @@ def kernel_traffic(kernel_file: str, units_per_launch: float):
 
 
 # ---------------------------------------------------------------------------- serving
-def serve_mixed(local, tio_burst, tio_ch, capacity, steps, overlap=False):
+def serve_mixed(local, tio_burst, tio_ch, capacity, steps, mode=2):
     """Open-loop serving: Poisson arrivals of bursts from three NVST-shaped
     channels (TiO and G-band 2560x2160 with 256^2 subfields, H-alpha 1024^2
     with 128^2 subfields), admitted into the engine (120 GB budget) as slots
@@ -267,7 +271,7 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps, overlap=False):
     frames = [torch.from_numpy(tio_burst["frames"]).pin_memory(), None,
               torch.from_numpy(hb["frames"]).pin_memory()]
     frames[1] = frames[0]
-    eng = Engine(chans, hbm_budget_bytes=int(120e9), max_inflight=3, device=local, overlap_kernels=overlap)
+    eng = Engine(chans, hbm_budget_bytes=int(120e9), max_inflight=3, device=local, overlap_kernels=mode)
     outs = {c: [torch.empty((chans[c].H, chans[c].W), dtype=torch.float32).pin_memory() for _ in range(3)]
             for c in range(3)}
     # warm up every channel once
@@ -311,8 +315,56 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps, overlap=False):
             "realised_arrival_rate": round(n / float(arrive[-1]), 3), "bursts": n, "channels": "TiO 2560x2160, G-band 2560x2160, H-alpha 1024x1024 (uniform mix)",
             "latency_ms_p50": round(1000 * float(np.percentile(lat, 50)), 1),
             "latency_ms_p99": round(1000 * float(np.percentile(lat, 99)), 1),
-            "nvst_rate_bursts_per_s": 0.3, "kernel_order": "concurrent" if overlap else "submission",
+            "nvst_rate_bursts_per_s": 0.3, "kernel_order": MODE_NAMES[mode],
             "note": "Poisson arrivals at 60% of the measured e2e capacity; latency = arrival to mosaic on host"}
+
+
+# ---------------------------------------------------------------------------- batched
+def run_batched(torch, plan, frames, spec, F, n_sub, info, args, stream, peak):
+    """args.batch bursts (the same synthetic burst in separate workspaces) per
+    step through sm_batch_reconstruct; also the persistent spectra +
+    bispectrum launch alone, timed with CUDA events on the launching stream."""
+    from paper_1701_00581_gb300 import SM_U16, Batch
+    nb = args.batch
+    items = []
+    for _ in range(nb):
+        ws, lay = plan.workspace(F, n_sub)
+        out = torch.empty((spec.H, spec.W), dtype=torch.float32, device=frames.device)
+        items.append({"frames": frames, "ws": ws, "lay": lay, "out": out})
+    bt = Batch([plan] * nb, [F] * nb, [SM_U16] * nb)
+    for _ in range(args.warmup):
+        bt.reconstruct(items, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bt.reconstruct(items, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ok = bt.status() == 0
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(args.steps):
+        bt.spectra_bispectrum(items, stream)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kms = k0.elapsed_time(k1) / args.steps
+    ok = ok and bt.status() == 0
+    triples = info["n_pairs"] * F * n_sub * nb
+    ach = FLOPS_PER_TRIPLE * triples / (kms / 1000.0) / 1e12
+    rec = {"value": round(nb * args.steps / (ms / 1000.0), 4), "unit": "bursts/s", "bursts_per_launch": nb,
+           "ms_per_burst": round(ms / (nb * args.steps), 3), "status_ok": ok,
+           "fused_launch_ms": round(kms, 3), "fused_launch_ms_per_burst": round(kms / nb, 3),
+           "fused_launch_items": bt.info["n_items"], "fused_launch_ctas": bt.info["grid"],
+           "fused_roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                              "frac": round(ach / peak, 4),
+                              "note": "bispectrum flops only (14 x used triples); the launch also does every FFT"},
+           "note": f"{nb} copies of the burst in separate workspaces per persistent spectra + bispectrum launch, "
+                   "then each burst's remaining stages; inputs resident in HBM"}
+    bt.close()
+    del items
+    return rec
 
 
 # ---------------------------------------------------------------------------- ranks
@@ -469,12 +521,20 @@ def main():
                      "note": "sm_reconstruct one burst at a time, copies not overlapped"}
         del dframes, host_frames
 
+    del ws, stf                              # the plain path's workspace (stf is a view of it)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    # batched: args.batch bursts per step through one persistent spectra +
+    # bispectrum launch (sm_batch_reconstruct), inputs resident in HBM
+    batched = None
+    if args.batch > 0:
+        batched = run_batched(torch, plan, frames, spec, F, n_sub, info, args, stream, peak)
+        torch.cuda.empty_cache()
+
     # end to end through the serving API, host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        del ws, stf                          # the plain path's workspace (stf is a view of it)
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
         host_frames = torch.from_numpy(b["frames"]).pin_memory()
         K_IN = max(1, args.inflight)
         host_out = [torch.empty((spec.H, spec.W), dtype=torch.float32).pin_memory() for _ in range(K_IN)]
@@ -482,7 +542,7 @@ def main():
         # the paper's layout needs a 123 GB workspace for one TiO burst
         budget_gb = 200 if args.layout == "paper" else 120
         eng = Engine([ch], hbm_budget_bytes=int(budget_gb * 1e9), max_inflight=K_IN, device=local,
-                     overlap_kernels=args.overlap)
+                     overlap_kernels=args.mode)
         fr_np = host_frames.numpy()
 
         stages = []
@@ -519,12 +579,12 @@ def main():
                "latency_ms_p50": 1000 * float(np.percentile(lat, 50)),
                "latency_ms_p99": 1000 * float(np.percentile(lat, 99)),
                "max_inflight": K_IN, "hbm_budget_gb": budget_gb,
-               "kernel_order": "concurrent" if args.overlap else "submission",
+               "kernel_order": MODE_NAMES[args.mode],
                "stage_ms": {k: round(float(np.mean([st[k] for st in stages])), 3) for k in stages[0]}}
 
     serving = None
     if not args.no_serve and args.workload == "tio2560" and not args.size:
-        serving = serve_mixed(local, b, ch, e2e["value"] if e2e else value, args.steps, args.overlap)
+        serving = serve_mixed(local, b, ch, e2e["value"] if e2e else value, args.steps, args.mode)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -555,7 +615,8 @@ def main():
                            "l2": "inputs larger than L2 (no flush)",
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": launches_per_step * args.steps,
-                "roofline": roofline, "clocks": clocks, "e2e": e2e, "plain_e2e": plain_e2e, "serving": serving,
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "plain_e2e": plain_e2e, "batched": batched,
+                "serving": serving,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -317,6 +317,87 @@ int sm_reconstruct(const sm_plan* plan, const void* frames, int frame_type, int 
 int sm_reconstruct_noalloc(const sm_plan* plan, const void* frames, int frame_type, int F,
                            const double* stf, float* out, uint8_t* valid, void* stream);
 
+/* ======================================================================== *
+ *  Batched launch: the subfields of several bursts -- of one channel or of  *
+ *  several, with subfields of different sizes -- through one persistent     *
+ *  launch of the spectra (Sect. 2: the Fourier transform of every           *
+ *  subimage) and the mean bispectrum (Sect. 2, 3.2: speckle masking), then  *
+ *  each burst's remaining stages.  The subfields are independent (Sect. 2), *
+ *  so a burst's result is bitwise the same alone or in any batch.           *
+ * ======================================================================== */
+typedef struct sm_batch sm_batch;
+
+/* One burst of a batch run.  Device pointers on the batch's device. */
+typedef struct {
+    const void*                frames;  /* [F][H][W] of the burst's frame_type   */
+    const double*              stf;     /* [N][N] centred model STF, or NULL: the
+                                           seeing is estimated from the burst
+                                           (Sect. 3.1, sm_stage_seeing)          */
+    void*                      ws;      /* the burst's workspace, 256-B aligned   */
+    const sm_workspace_layout* lay;     /* sm_workspace_query(plan, F, n_sub):
+                                           every subfield in one chunk           */
+    float*                     out;     /* [H][W] mosaic                          */
+    uint8_t*                   valid;   /* [H][W] or NULL                         */
+} sm_batch_io;
+
+#define SM_BATCH_FUSED 1
+#define SM_BATCH_TILES 2
+#define SM_BATCH_GRID  3
+
+/* Shape of the batched launch; a field left 0 takes the tuned value for the
+ * batch's largest subfield size N and its R (the table the library's
+ * autotuner wrote, autotune.py).                                            */
+typedef struct {
+    int lookahead;      /* subfields whose transforms run ahead of the tiles  */
+    int ctas_per_sm;    /* persistent CTAs per SM: 3 (168 registers a thread)
+                           or 4 (128)                                          */
+    int launch;         /* SM_BATCH_FUSED: one persistent launch whose items
+                           are the transforms and the tiles; SM_BATCH_TILES:
+                           the transforms first (per-stage spectra kernel),
+                           then one persistent launch of the tiles;
+                           SM_BATCH_GRID: the transforms first, then one grid
+                           of CTAs over every tile of every burst (scheduled
+                           by the hardware, not a queue)                      */
+    int tile_order;     /* order of a subfield's tiles in the queue: 1 as the
+                           plan lists them (by target block), 2 costliest
+                           first                                               */
+} sm_batch_opts;
+
+/* Build the work queue of a batch of n (1..8) bursts: burst i has the plan
+ * plans[i], F[i] frames of frame_type[i].  The plans may differ (channel,
+ * frame size, N, R) but share the device and the spectra precision, and
+ * accumulate plain FP32 sums (SM_ACC_PLAIN).  The queue holds one item per
+ * (burst, subfield, frame) transform (SM_BATCH_FUSED) and per (burst,
+ * subfield, tile) of the bispectrum (SM_BATCH_FUSED, SM_BATCH_TILES); a
+ * subfield's transforms come `lookahead` subfields ahead of its tiles.  The
+ * SM_BATCH_GRID launch needs no queue.  opts may be NULL
+ * (all tuned).  Allocates the queue, the dependency counters and a
+ * transform scratch tile per persistent CTA on the device (sm_batch_info
+ * reports the bytes); SM_EINVAL on a bad batch.                             */
+int sm_batch_create(int n, const sm_plan* const* plans, const int* F, const int* frame_type,
+                    const sm_batch_opts* opts, sm_batch** out);
+/* The shape the batch was built with (the tuned values filled in).         */
+int sm_batch_get_opts(const sm_batch* bt, sm_batch_opts* opts);
+int sm_batch_destroy(sm_batch* bt);
+/* Items in the queue, persistent CTAs of the launch, device bytes held.    */
+int sm_batch_info(const sm_batch* bt, int* n_items, int* grid, size_t* device_bytes);
+
+/* The batched transforms and bispectrum alone: spectra, flux and mean of
+ * every subfield of every burst, and the bispectrum, into each burst's
+ * workspace.  io: [n].  Asynchronous on `stream`; capturable in a CUDA
+ * graph.  In SM_BATCH_FUSED a bispectrum tile waits for its subfield's F
+ * transforms with a bounded poll; if a wait ever gives up, the tile is
+ * skipped and sm_batch_status reports it.                                  */
+int sm_batch_spectra_bispectrum(sm_batch* bt, const sm_batch_io* io, void* stream);
+/* The whole path for every burst of the batch: the persistent launch, then
+ * per burst P/M/noise, the seeing estimate when io[i].stf is NULL, the
+ * modulus (Eq. 1), the photon-noise correction when the channel asks for it,
+ * the phase, the inverse transforms and the mosaic.  Asynchronous.         */
+int sm_batch_reconstruct(sm_batch* bt, const sm_batch_io* io, void* stream);
+/* Status of the last run's persistent launch, after the caller has
+ * synchronised its stream: SM_OK, or SM_ECUDA when a dependency wait gave up. */
+int sm_batch_status(const sm_batch* bt);
+
 /* Model STF (Sect. 3.2, calibrated by r0): per frame
  * T0^2 exp(-6.88 (rho D/r0)^(5/3)) + ck (r0/D)^2 T0, averaged over the F
  * frames' D/r0 and normalised to 1 at k = 0.  Host only; stf_out is host
@@ -344,7 +425,18 @@ typedef struct {
                                            in submission order, one burst at a
                                            time, while the next bursts' frame
                                            copies proceed on their own streams;
-                                           1: bursts' kernels run concurrently */
+                                           1: bursts' kernels run concurrently;
+                                           2: pipelined -- two whole-burst
+                                           workspaces; the bursts' transforms
+                                           and bispectra run in submission
+                                           order, and each burst's phase,
+                                           inverse and mosaic run on a
+                                           high-priority stream beside the
+                                           next burst's transforms and
+                                           bispectrum (the recursion takes a
+                                           quarter of an SM and fills the
+                                           issue slots the ALU-bound
+                                           bispectrum leaves)                 */
     /* Optional device allocator for the engine's one arena of
      * hbm_budget_bytes (both NULL: cudaMalloc / cudaFree).  dev_alloc is
      * called once by sm_open and must return device memory of `device`
@@ -403,9 +495,11 @@ typedef struct {
  * channel's max_frames and the largest subfield chunk that leaves room for
  * max_inflight bursts' own buffers (frames, mosaic, mask, STF table); with
  * overlap_kernels = 1 each burst holds its own workspace in an equal share
- * of the budget.  SM_ENOMEM when the budget cannot hold one subfield's
- * workspace beside those buffers (shared workspace), or at submit when one
- * burst does not fit its share.  *out is NULL on any failure.               */
+ * of the budget; with 2 the arena starts with two whole-burst workspaces
+ * (SM_ENOMEM when they and the bursts' buffers do not fit).  SM_ENOMEM when
+ * the budget cannot hold one subfield's workspace beside those buffers
+ * (shared workspace), or at submit when one burst does not fit its share.
+ * *out is NULL on any failure.                                               */
 int sm_open(const sm_config* cfg, sm_handle** out);
 /* sm_submit_burst: stage one burst (Sect. 2: the frames of one burst of one
  * channel) -- copies the frames to the device (the caller may reuse them on
@@ -420,10 +514,14 @@ int sm_open(const sm_config* cfg, sm_handle** out);
 int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket);
 /* sm_poll: the mosaic of one burst (Sect. 3.2: the merged image) -- wait
  * up to timeout_ms (0 = test and return SM_PENDING, > 0 = return SM_ETIMEDOUT
- * when it elapses, < 0 = forever).  SM_OK once the mosaic (and mask) have been
- * copied into the burst's out (and valid) buffers; res gets the latency
- * record and per-stage device times; then the ticket is released.  A ticket
- * whose work failed reports that status once and is released.              */
+ * when it elapses, < 0 = forever).  SM_OK once the mosaic (and mask) are in
+ * the burst's out (and valid) buffers; res gets the latency record and
+ * per-stage device times; then the ticket is released.  The device copies
+ * the results back at the end of the burst's own work: straight into out
+ * and valid when they are page-locked host memory (so they may change while
+ * the ticket is pending), otherwise into a pinned staging buffer from which
+ * this call copies them.  A ticket whose work failed reports that status
+ * once and is released.                                                      */
 int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result* res);
 /* sm_close: end the engine -- cancel pending tickets, wait for the device,
  * free everything.  (The paper's master process ends after the mosaic is

@@ -13,12 +13,12 @@ from typing import Dict, Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_EDGE_DROP, SM_EDGE_PAD, SM_F32,  # noqa: F401
+from ._lib import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BATCH_FUSED, SM_BATCH_GRID, SM_BATCH_TILES, SM_BF16, SM_EDGE_DROP, SM_EDGE_PAD, SM_F32,  # noqa: F401
                    SM_FP16, SM_FP32, SM_MOSAIC_BLEND, SM_MOSAIC_CENTRAL,
                    SM_PHASE_FP32, SM_PHASE_FP64, SM_U16, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT, SpeckleError,
                    check, load)
 
-__all__ = ["Channel", "Plan", "Engine", "load", "SpeckleError"]
+__all__ = ["Channel", "Plan", "Batch", "Engine", "load", "SpeckleError"]
 
 
 @dataclasses.dataclass
@@ -238,6 +238,67 @@ def _frame_type(frames) -> int:
     return SM_U16 if str(frames.dtype).endswith("uint16") else SM_F32
 
 
+class Batch:
+    """sm_batch: several bursts' spectra and bispectra in one persistent launch.
+
+    ``plans``: one Plan per burst (channels may differ); ``F`` and
+    ``frame_types`` per burst.  The work queue is built once here."""
+
+    def __init__(self, plans: Sequence[Plan], F: Sequence[int], frame_types: Sequence[int], lookahead: int = 0,
+                 ctas_per_sm: int = 0, launch: int = 0, tile_order: int = 0):
+        """0 for an option takes the tuned value (sm_batch_opts)."""
+        self.lib = load()
+        self.plans = list(plans)
+        n = len(self.plans)
+        arr = (C.c_void_p * n)(*[p.h.value for p in self.plans])
+        Fs = (C.c_int * n)(*F)
+        fts = (C.c_int * n)(*frame_types)
+        h = C.c_void_p()
+        opts = _lib.sm_batch_opts(lookahead, ctas_per_sm, launch, tile_order)
+        check(self.lib.sm_batch_create(n, arr, Fs, fts, C.byref(opts), C.byref(h)), "sm_batch_create")
+        self.h = h
+        got = _lib.sm_batch_opts()
+        check(self.lib.sm_batch_get_opts(self.h, C.byref(got)), "sm_batch_get_opts")
+        self.opts = {"lookahead": got.lookahead, "ctas_per_sm": got.ctas_per_sm, "launch": got.launch,
+                     "tile_order": got.tile_order}
+        ni, grid, nb = C.c_int(), C.c_int(), C.c_size_t()
+        check(self.lib.sm_batch_info(self.h, C.byref(ni), C.byref(grid), C.byref(nb)), "sm_batch_info")
+        self.info = {"n_items": ni.value, "grid": grid.value, "device_bytes": nb.value}
+
+    def _io(self, items):
+        """items: per burst a dict with frames, ws, lay, out and optionally stf, valid."""
+        io = (_lib.sm_batch_io * len(items))()
+        self._keep = []
+        for i, it in enumerate(items):
+            lay = it["lay"]
+            self._keep.append(lay)
+            io[i] = _lib.sm_batch_io(_ptr(it["frames"]), _ptr(it.get("stf")), _ptr(it["ws"]), C.pointer(lay),
+                                     _ptr(it.get("out")), _ptr(it.get("valid")))
+        return io
+
+    def spectra_bispectrum(self, items, stream=None):
+        check(self.lib.sm_batch_spectra_bispectrum(self.h, self._io(items), _stream(stream)),
+              "sm_batch_spectra_bispectrum")
+
+    def reconstruct(self, items, stream=None):
+        check(self.lib.sm_batch_reconstruct(self.h, self._io(items), _stream(stream)), "sm_batch_reconstruct")
+
+    def status(self) -> int:
+        """SM_OK, or the error the last run recorded (synchronise the stream first)."""
+        return self.lib.sm_batch_status(self.h)
+
+    def close(self):
+        if self.h:
+            self.lib.sm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # sm_result.stage_ms, in order
 STAGE_NAMES = ("spectra", "stats", "seeing", "modulus", "bispectrum", "phase", "inverse", "mosaic")
 
@@ -246,9 +307,12 @@ class Engine:
     """sm_open / sm_submit_burst / sm_poll / sm_close (the serving engine)."""
 
     def __init__(self, channels: Sequence[Channel], hbm_budget_bytes: int, max_inflight: int = 2,
-                 device: int = 0, overlap_kernels: bool = False, allocator: Optional[str] = None):
-        """``allocator="torch"`` takes the engine's arena from torch's caching
-        allocator (one uint8 tensor held until close) instead of cudaMalloc."""
+                 device: int = 0, overlap_kernels: int = 0, allocator: Optional[str] = None):
+        """``overlap_kernels``: 0 the bursts' kernels in submission order, 1
+        concurrently, 2 pipelined (a burst's phase, inverse and mosaic beside
+        the next burst's transforms and bispectrum).  ``allocator="torch"``
+        takes the engine's arena from torch's caching allocator (one uint8
+        tensor held until close) instead of cudaMalloc."""
         self.lib = load()
         self._ch = (_lib.sm_channel * len(channels))(*[c.to_c() for c in channels])
         self.channels = list(channels)
@@ -273,7 +337,7 @@ class Engine:
             raise ValueError("allocator must be None or 'torch'")
         self._callbacks = (alloc, free)          # kept alive while the engine holds them
         cfg = _lib.sm_config(len(channels), self._ch, hbm_budget_bytes, max_inflight, device,
-                             1 if overlap_kernels else 0, alloc, free, None)
+                             int(overlap_kernels), alloc, free, None)
         h = C.c_void_p()
         check(self.lib.sm_open(C.byref(cfg), C.byref(h)), "sm_open")
         self.h = h

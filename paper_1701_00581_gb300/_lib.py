@@ -22,6 +22,7 @@ SM_ACC_PLAIN, SM_ACC_KAHAN = 0, 1
 SM_PHASE_FP32, SM_PHASE_FP64 = 0, 1
 SM_EDGE_PAD, SM_EDGE_DROP = 0, 1
 SM_MOSAIC_BLEND, SM_MOSAIC_CENTRAL = 0, 1
+SM_BATCH_FUSED, SM_BATCH_TILES, SM_BATCH_GRID = 1, 2, 3
 
 
 class sm_channel(C.Structure):
@@ -69,6 +70,15 @@ class sm_result(C.Structure):
                 ("stage_ms", C.c_double * 8)]
 
 
+class sm_batch_opts(C.Structure):
+    _fields_ = [("lookahead", C.c_int), ("ctas_per_sm", C.c_int), ("launch", C.c_int), ("tile_order", C.c_int)]
+
+
+class sm_batch_io(C.Structure):
+    _fields_ = [("frames", C.c_void_p), ("stf", C.c_void_p), ("ws", C.c_void_p),
+                ("lay", C.POINTER(sm_workspace_layout)), ("out", C.c_void_p), ("valid", C.c_void_p)]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _LAY = C.POINTER(sm_workspace_layout)
@@ -98,6 +108,14 @@ SIGNATURES = {
     "sm_reconstruct": (_I, [_P, _P, _I, _I, _P, _I, _P, _LAY, _P, _P, _P]),
     "sm_reconstruct_noalloc": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
     "sm_model_stf": (_I, [C.POINTER(sm_channel), _I, _P, _P]),
+    "sm_batch_create": (_I, [_I, C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(sm_batch_opts),
+                             C.POINTER(_P)]),
+    "sm_batch_get_opts": (_I, [_P, C.POINTER(sm_batch_opts)]),
+    "sm_batch_destroy": (_I, [_P]),
+    "sm_batch_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+    "sm_batch_spectra_bispectrum": (_I, [_P, C.POINTER(sm_batch_io), _P]),
+    "sm_batch_reconstruct": (_I, [_P, C.POINTER(sm_batch_io), _P]),
+    "sm_batch_status": (_I, [_P]),
     "sm_open": (_I, [C.POINTER(sm_config), C.POINTER(_P)]),
     "sm_submit_burst": (_I, [_P, C.POINTER(sm_burst), C.POINTER(C.c_uint64)]),
     "sm_poll": (_I, [_P, C.c_uint64, _I, C.POINTER(sm_result)]),

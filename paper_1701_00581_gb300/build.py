@@ -21,8 +21,9 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libspeckle_gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["k_fft.cu", "k_small.cu", "k_bispec.cu", "k_phase.cu", "k_seeing.cu", "k_refine.cu", "k_front.cu", "sm_noalloc.cu"]
-CPP_SOURCES = ["sm_plan.cpp", "sm_api.cpp"]
+CU_SOURCES = ["k_bispec.cu", "k_batch.cu", "k_fft.cu", "k_phase.cu", "k_small.cu", "k_seeing.cu", "k_refine.cu",
+              "k_front.cu", "sm_noalloc.cu"]
+CPP_SOURCES = ["sm_plan.cpp", "sm_api.cpp", "sm_batch.cpp"]
 
 
 def _nvcc() -> str:
@@ -34,7 +35,7 @@ def _nvcc() -> str:
 
 def _headers():
     hs = [os.path.join(INCLUDE, "speckle.h")]
-    hs += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hs += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     return hs
 
 

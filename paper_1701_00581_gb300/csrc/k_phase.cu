@@ -22,8 +22,12 @@ using smi::PlanDev;
 using smi::TILE_PAIRS;
 using smi::TILE_V;
 
-constexpr int PH_THREADS = 512;
-constexpr int PH_WARPS = PH_THREADS / 32;
+// Items are spread over 16 virtual warps whatever the CTA size: each item
+// then lands in the same slot of the same batch, and its sum runs along the
+// same shuffle tree, in the 512-thread kernel (two CTAs per SM, the stage
+// path) and in the 256-thread one (64 registers a thread, so it fits beside
+// three bispectrum CTAs on an SM): the two give bitwise the same phasors.
+constexpr int PH_VWARPS = 16;
 
 // Complex values of the recursion's arithmetic type T.
 template <typename T> struct Cx;
@@ -96,10 +100,11 @@ __host__ __device__ inline size_t phase_layout(int hb_rows, int pitch, int mri, 
     return o;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PH_THREADS, sizeof(T) == 4 ? 2 : 1)
+template <typename T, int TH>
+__global__ void __launch_bounds__(TH, TH == 512 ? (sizeof(T) == 4 ? 2 : 1) : 4)
 k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, const float* __restrict__ P,
         double2* __restrict__ z) {
+    constexpr int PH_THREADS = TH, PH_WARPS = TH / 32;
     using T2 = typename Cx<T>::T2;
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K, pitch = p.box_pitch;
@@ -160,7 +165,7 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
         okm = 0;
 #pragma unroll
         for (int q = 0; q < PH_ITEMS; ++q) {
-            const int e = base + q * PH_WARPS;
+            const int e = base + q * PH_VWARPS;
             bv[q] = make_float2(0.f, 0.f);
             pk[q] = 0;
             if (e < ni) {
@@ -190,8 +195,13 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
         const int npn = more ? p.ring_start[r + 2] - p.ring_start[r + 1] : 0;
         stage(r + 1);
         // (1) items: products in T, one term per lane, item sums in T
-        for (int base = warp; base < ni; base += PH_WARPS * PH_ITEMS) {
-            if (base != warp) load_batch(p.items + i0, base, ni);
+        for (int job = 0, vw = warp, base = warp; vw < PH_VWARPS; ++job) {
+            if (base >= ni) {                    // this virtual warp is done: the next one
+                vw += PH_WARPS;
+                base = vw;
+                continue;
+            }
+            if (job != 0) load_batch(p.items + i0, base, ni);
             T2 t[PH_ITEMS];
 #pragma unroll
             for (int q = 0; q < PH_ITEMS; ++q) {
@@ -227,8 +237,9 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
                 }
             }
             const T2 sum = reduce8(t, lane);
-            const int e = base + (lane >> 2) * PH_WARPS;
+            const int e = base + (lane >> 2) * PH_VWARPS;
             if ((lane & 3) == 0 && e < ni) part[e] = sum;
+            base += PH_VWARPS * PH_ITEMS;
         }
         asm volatile("cp.async.wait_group 0;");
         __syncthreads();                          // partials complete, ring r+1 records visible
@@ -285,16 +296,21 @@ size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_
 }
 
 cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M, const float* P,
-                         double2* z, cudaStream_t st) {
+                         double2* z, cudaStream_t st, int threads) {
     const size_t sm = phase_smem_bytes(p.hb_rows, p.box_pitch, p.max_ring_items, p.max_ring_points, p.phase_prec);
+    cudaError_t e;
     if (p.phase_prec == SM_PHASE_FP64) {
-        cudaError_t e = cudaFuncSetAttribute(k_phase<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute(k_phase<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_phase<double><<<nsub, PH_THREADS, sm, st>>>(p, B, M, P, z);
+        k_phase<double, 512><<<nsub, 512, sm, st>>>(p, B, M, P, z);
+    } else if (threads == 256) {
+        e = cudaFuncSetAttribute(k_phase<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_phase<float, 256><<<nsub, 256, sm, st>>>(p, B, M, P, z);
     } else {
-        cudaError_t e = cudaFuncSetAttribute(k_phase<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute(k_phase<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_phase<float><<<nsub, PH_THREADS, sm, st>>>(p, B, M, P, z);
+        k_phase<float, 512><<<nsub, 512, sm, st>>>(p, B, M, P, z);
     }
     return cudaGetLastError();
 }

@@ -341,9 +341,25 @@ int reconstruct_check(const sm_plan* plan, int F, const double* stf, int nsub_ch
 
 // Run a schedule; with `marks`, marks[i] is recorded on the stream before
 // call i and marks[calls.size()] after the last (timing of each call).
+// The phase stage with the recursion kernel at `threads` threads a CTA (512:
+// the stage path; 256: small enough to share an SM with three bispectrum
+// CTAs; bitwise the same phasors).
+int stage_phase_threads(const sm_plan* plan, int nsub, void* ws, const sm_workspace_layout* lay, void* stream,
+                        int threads) {
+    if (threads == 512 || plan->dev.phase_prec != SM_PHASE_FP32) return sm_stage_phase(plan, nsub, ws, lay, stream);
+    DeviceGuard g(plan->device);
+    int rc = ret(smk::launch_phase(plan->dev, nsub, at<float2>(ws, lay->B), at<float2>(ws, lay->M),
+                                   at<float>(ws, lay->P), at<double2>(ws, lay->z), (cudaStream_t)stream, threads),
+                 "phase kernel");
+    if (rc || plan->dev.phase_iters == 0) return rc;
+    return ret(smk::launch_refine(plan->dev, nsub, at<float2>(ws, lay->B), at<float>(ws, lay->P),
+                                  at<double2>(ws, lay->z), at<float2>(ws, lay->refine), (cudaStream_t)stream),
+               "least-squares phase sweeps");
+}
+
 int run_schedule(const sm_plan* plan, const std::vector<StageCall>& calls, const void* frames, int frame_type,
                  int F, const double* stf, void* ws, const sm_workspace_layout* lay, float* out, uint8_t* valid,
-                 void* stream, const std::vector<cudaEvent_t>* marks) {
+                 void* stream, const std::vector<cudaEvent_t>* marks, int phase_threads = 512) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto mark = [&](size_t i) -> int {
         if (!marks) return SM_OK;
@@ -360,7 +376,7 @@ int run_schedule(const sm_plan* plan, const std::vector<StageCall>& calls, const
         case ST_SEEING_STF: rc = sm_stage_seeing_stf(plan, ws, lay, stream); break;
         case ST_AMPLITUDE: rc = sm_stage_amplitude(plan, c.ns, stf, ws, lay, stream); break;
         case ST_BISPECTRUM: rc = sm_stage_bispectrum(plan, F, c.ns, ws, lay, stream); break;
-        case ST_PHASE: rc = sm_stage_phase(plan, c.ns, ws, lay, stream); break;
+        case ST_PHASE: rc = stage_phase_threads(plan, c.ns, ws, lay, stream, phase_threads); break;
         case ST_INVERSE: rc = sm_stage_inverse(plan, F, c.s0, c.ns, ws, lay, stream); break;
         case ST_MOSAIC: rc = sm_stage_mosaic(plan, ws, lay, out, valid, stream); break;
         }
@@ -443,8 +459,23 @@ struct Job {
     const double* d_seeing = nullptr;     // the burst's D / mean r0 when estimated
     double* d_seeing_io = nullptr;        // its copy in the burst's own buffers (shared workspace)
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_mid = nullptr;         // pipelined: the burst's front half done
     const std::vector<cudaEvent_t>* marks = nullptr;   // the burst graph's stage marks
     const std::vector<int>* mark_stage = nullptr;
+    const std::vector<cudaEvent_t>* marks2 = nullptr;  // pipelined: the back half's marks
+    const std::vector<int>* mark_stage2 = nullptr;
+    const std::vector<cudaEvent_t>* marks3 = nullptr;  // pipelined: the bispectrum's marks
+    const std::vector<int>* mark_stage3 = nullptr;
+    cudaEvent_t ev_bis = nullptr;         // pipelined: the burst's bispectrum done
+    // pipelined: the back half is launched later (next submit or poll)
+    bool back_pending = false;
+    sm_burst bcopy{};
+    const void* d_frames = nullptr;
+    const double* d_stf = nullptr;
+    void* ws = nullptr;
+    sm_workspace_layout lay{};
+    int wsi = 0;
+    bool staged = false;                  // the mosaic went to the slot's pinned staging, not to out
     double t_submit = 0.0;
     int status = SM_PENDING;
 };
@@ -490,6 +521,23 @@ struct sm_handle {
     void* shared_ws = nullptr;
     size_t shared_ws_bytes = 0;
     size_t arena_bytes = 0;               // what the bursts' arena holds
+    // Pipelined (overlap_kernels = 2): two workspaces, bursts alternating;
+    // each burst's front half (transforms .. bispectrum) after the previous
+    // burst's front half and after the back half of the burst that used the
+    // workspace before; the back half (phase .. mosaic) on a high-priority
+    // stream beside the next burst's front half.
+    int mode = 0;
+    void* ws2[2] = {nullptr, nullptr};
+    cudaEvent_t ev_front = nullptr, ev_free[2] = {nullptr, nullptr};
+    bool front_recorded = false, free_recorded[2] = {false, false};
+    uint64_t n_launched = 0;
+    uint64_t pending_back = 0;            // ticket whose back half waits for the next burst (0: none)
+    std::vector<cudaStream_t> pstreams;   // per slot, middle priority (pipelined back halves)
+    std::vector<cudaStream_t> lstreams;   // per slot, lowest priority (pipelined bispectra)
+    // Per slot: pinned staging for the mosaic, mask and seeing value, copied
+    // back on the burst's own stream so that sm_poll need not wait for it.
+    std::vector<char*> pin_out;
+    size_t pin_out_bytes = 0;
     // Host-side failure injection (SM_FAULT=alloc:N at sm_open): admission
     // number fault_alloc_at (from 1) fails as if its arena allocation had.
     long long fault_alloc_at = 0;
@@ -530,7 +578,9 @@ size_t burst_bytes(const sm_handle* h, int c, int F, sm_workspace_layout* lay) {
 void finish_job(sm_handle* h, Job& j) {
     if (j.ev_start) cudaEventDestroy(j.ev_start);
     if (j.ev_done) cudaEventDestroy(j.ev_done);
-    j.ev_start = j.ev_done = nullptr;
+    if (j.ev_mid) cudaEventDestroy(j.ev_mid);
+    if (j.ev_bis) cudaEventDestroy(j.ev_bis);
+    j.ev_start = j.ev_done = j.ev_mid = j.ev_bis = nullptr;
     if (j.bytes) h->arena.release(j.off, j.bytes);
     j.bytes = 0;
     if (j.slot >= 0) h->stream_busy[j.slot] = false;
@@ -545,10 +595,13 @@ namespace {
 // CUDA graph (captured on first use of the key).  The frame type and the
 // STF mode (given, or estimated on the device when d_stf is NULL) are part
 // of the captured kernels, so they join the key through the F slot.
+// part 0: the whole schedule; pipelined: 1 the stages before the bispectrum,
+// 3 the bispectrum, 2 the back half (phase .. mosaic, with the 256-thread
+// phase kernel); wsi: the pipelined workspace the burst uses.
 int launch_burst(sm_handle* h, const sm_burst* b, Job& j, const void* d_frames, const double* d_stf,
-                 void* ws, sm_workspace_layout& lay, cudaStream_t st) {
+                 void* ws, sm_workspace_layout& lay, cudaStream_t st, int part = 0, int wsi = 0) {
     const auto key = std::make_tuple(b->channel, b->F * 4 + (d_stf ? 0 : 2) + (b->frame_type == SM_F32 ? 1 : 0),
-                                     j.off, j.slot);
+                                     j.off, j.slot * 16 + part * 4 + wsi);
     sm_handle::Graph* g = nullptr;
     {
         std::lock_guard<std::mutex> lk(h->mu);
@@ -560,7 +613,17 @@ int launch_burst(sm_handle* h, const sm_burst* b, Job& j, const void* d_frames, 
         const double* stf_used = nullptr;
         int rc = reconstruct_check(plan, b->F, d_stf, h->chunk[b->channel], ws, &lay, &stf_used);
         if (rc) return rc;
-        const std::vector<StageCall> calls = burst_schedule(plan, d_stf == nullptr, h->chunk[b->channel]);
+        std::vector<StageCall> calls = burst_schedule(plan, d_stf == nullptr, h->chunk[b->channel]);
+        if (part) {
+            // the schedule of an unchunked burst, cut before the bispectrum
+            // and before the phase
+            size_t cb = 0, cp = 0;
+            while (cb < calls.size() && calls[cb].stage != ST_BISPECTRUM) ++cb;
+            while (cp < calls.size() && calls[cp].stage != ST_PHASE) ++cp;
+            if (part == 1) calls = std::vector<StageCall>(calls.begin(), calls.begin() + cb);
+            else if (part == 3) calls = std::vector<StageCall>(calls.begin() + cb, calls.begin() + cp);
+            else calls = std::vector<StageCall>(calls.begin() + cp, calls.end());
+        }
         sm_handle::Graph ng;
         for (const StageCall& c : calls) ng.stage.push_back(reported_stage(c.stage));
         ng.marks.assign(calls.size() + 1, nullptr);
@@ -575,8 +638,8 @@ int launch_burst(sm_handle* h, const sm_burst* b, Job& j, const void* d_frames, 
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { drop(nullptr); return cuda_fail(e, "cudaStreamBeginCapture"); }
         rc = run_schedule(plan, calls, d_frames, b->frame_type, b->F, stf_used, ws, &lay, j.d_out, j.d_valid, st,
-                          &ng.marks);
-        if (rc == SM_OK && j.d_seeing_io)
+                          &ng.marks, part == 2 ? 256 : 512);
+        if (rc == SM_OK && j.d_seeing_io && (part == 0 || part == 2))
             rc = ret(cudaMemcpyAsync(j.d_seeing_io, j.d_seeing, sizeof(double), cudaMemcpyDeviceToDevice, st),
                      "cudaMemcpyAsync(seeing)");
         cudaGraph_t graph = nullptr;
@@ -589,9 +652,66 @@ int launch_burst(sm_handle* h, const sm_burst* b, Job& j, const void* d_frames, 
         std::lock_guard<std::mutex> lk(h->mu);
         g = &(h->graphs[key] = std::move(ng));
     }
-    j.marks = &g->marks;
-    j.mark_stage = &g->stage;
+    if (part == 2) {
+        j.marks2 = &g->marks;
+        j.mark_stage2 = &g->stage;
+    } else if (part == 3) {
+        j.marks3 = &g->marks;
+        j.mark_stage3 = &g->stage;
+    } else {
+        j.marks = &g->marks;
+        j.mark_stage = &g->stage;
+    }
     return ret(cudaGraphLaunch(g->exec, st), "cudaGraphLaunch");
+}
+
+// The burst's results back to the host on its own stream: straight into the
+// caller's buffers when they are page-locked host memory, otherwise into the
+// slot's pinned staging, which sm_poll copies out.  The seeing value always
+// goes to the staging.
+int copy_back(sm_handle* h, Job& j, const sm_channel& ch, cudaStream_t st) {
+    const size_t npx = (size_t)ch.W * ch.H;
+    char* pin = h->pin_out[j.slot];
+    auto pinned = [](const void* p) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return a.type == cudaMemoryTypeHost;
+    };
+    j.staged = !pinned(j.host_out) || (j.host_valid && !pinned(j.host_valid));
+    float* out = j.staged ? reinterpret_cast<float*>(pin) : j.host_out;
+    uint8_t* valid = j.staged ? reinterpret_cast<uint8_t*>(pin + al(npx * 4)) : j.host_valid;
+    cudaError_t e = cudaMemcpyAsync(out, j.d_out, npx * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && j.host_valid) e = cudaMemcpyAsync(valid, j.d_valid, npx, cudaMemcpyDeviceToHost, st);
+    double* sv = reinterpret_cast<double*>(pin + al(npx * 4) + al(npx));
+    *sv = 0.0;
+    if (e == cudaSuccess && j.d_seeing)
+        e = cudaMemcpyAsync(sv, j.d_seeing_io ? j.d_seeing_io : j.d_seeing, sizeof(double), cudaMemcpyDeviceToHost, st);
+    return ret(e, "copying the mosaic back");
+}
+
+// A pipelined burst's back half (phase .. mosaic and the copies back) on its
+// slot's middle-priority stream, after its bispectrum and after `after` (the
+// next burst's stages before the bispectrum, so that the spectra kernel,
+// which takes whole SMs, does not wait for phase CTAs; or nullptr).  The
+// caller holds launch_mu but not mu.
+int launch_back(sm_handle* h, Job& j, cudaEvent_t after) {
+    cudaStream_t ph = h->pstreams[j.slot];
+    j.back_pending = false;
+    cudaError_t e = cudaStreamWaitEvent(ph, j.ev_bis, 0);
+    if (e == cudaSuccess && after) e = cudaStreamWaitEvent(ph, after, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering burst");
+    int rc = launch_burst(h, &j.bcopy, j, j.d_frames, j.d_stf, j.ws, j.lay, ph, 2, j.wsi);
+    if (rc == SM_OK) {
+        e = cudaEventRecord(h->ev_free[j.wsi], ph);
+        h->free_recorded[j.wsi] = e == cudaSuccess;
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
+    }
+    if (rc == SM_OK) rc = copy_back(h, j, h->ch[j.channel], ph);
+    if (rc == SM_OK) rc = ret(cudaEventRecord(j.ev_done, ph), "cudaEventRecord");
+    return rc;
 }
 
 }  // namespace
@@ -625,7 +745,14 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
     // largest count that does.  Concurrent kernels: each burst's workspace
     // and buffers in an equal share of the budget.  In order: one shared
     // workspace beside max_inflight bursts' own buffers.
-    const bool shared = !cfg->overlap_kernels;
+    if (cfg->overlap_kernels < 0 || cfg->overlap_kernels > 2) {
+        for (auto* q : h->plans) sm_plan_destroy(q);
+        delete h;
+        set_error("overlap_kernels must be 0, 1 or 2");
+        return SM_EINVAL;
+    }
+    h->mode = cfg->overlap_kernels;
+    const bool shared = h->mode != 1;
     size_t io_max = 0;
     for (int c = 0; c < cfg->n_channels; ++c) io_max = std::max(io_max, io_bytes(h, c, h->ch[c].max_frames));
     const size_t io_all = io_max * (size_t)cfg->max_inflight;
@@ -647,10 +774,22 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
             if (fits(mid)) lo = mid; else hi = mid - 1;
         }
         h->chunk[c] = lo;
-        if (shared) {
+        if (h->mode == 2) {
+            // two unchunked workspaces (a burst's back half reads its whole
+            // workspace while the next burst's front half fills the other)
+            h->chunk[c] = p->dev.n_sub;
+            sm_workspace_query(p, h->ch[c].max_frames, p->dev.n_sub, &lay);
+            h->shared_ws_bytes = std::max(h->shared_ws_bytes, 2 * al(lay.bytes));
+        } else if (shared) {
             sm_workspace_query(p, h->ch[c].max_frames, lo, &lay);
             h->shared_ws_bytes = std::max(h->shared_ws_bytes, al(lay.bytes));
         }
+    }
+    if (h->mode == 2 && h->shared_ws_bytes + io_all > cfg->hbm_budget_bytes) {
+        for (auto* q : h->plans) sm_plan_destroy(q);
+        delete h;
+        set_error("pipelined mode: hbm_budget_bytes cannot hold two whole-burst workspaces and the bursts' buffers");
+        return SM_ENOMEM;
     }
     if (shared && h->shared_ws_bytes + io_all > cfg->hbm_budget_bytes) {
         for (auto* q : h->plans) sm_plan_destroy(q);
@@ -679,15 +818,37 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
     }
     h->arena_bytes = cfg->hbm_budget_bytes - h->shared_ws_bytes;
     h->shared_ws = shared ? h->dmem : nullptr;
+    if (h->mode == 2) {
+        h->ws2[0] = h->dmem;
+        h->ws2[1] = static_cast<char*>(h->dmem) + h->shared_ws_bytes / 2;
+    }
     h->arena.init(static_cast<char*>(h->dmem) + h->shared_ws_bytes, h->arena_bytes);
     e = cudaEventCreateWithFlags(&h->order, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_front, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[1], cudaEventDisableTiming);
     if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaEventCreate"); }
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    for (const auto& c : h->ch)
+        h->pin_out_bytes = std::max(h->pin_out_bytes, al((size_t)c.W * c.H * 4) + al((size_t)c.W * c.H) + 256);
     for (int i = 0; i < cfg->max_inflight; ++i) {
         cudaStream_t s;
-        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        e = h->mode == 2 ? cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio_hi)
+                         : cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaStreamCreate"); }
         h->streams.push_back(s);
         h->stream_busy.push_back(false);
+        cudaStream_t ps, ls;
+        e = cudaStreamCreateWithPriority(&ps, cudaStreamNonBlocking, (prio_hi + prio_lo) / 2);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ls, cudaStreamNonBlocking, prio_lo);
+        if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaStreamCreateWithPriority"); }
+        h->pstreams.push_back(ps);
+        h->lstreams.push_back(ls);
+        char* po = nullptr;
+        e = cudaHostAlloc((void**)&po, h->pin_out_bytes, cudaHostAllocDefault);
+        if (e != cudaSuccess) { *out = h; sm_close(h); *out = nullptr; return cuda_fail(e, "cudaHostAlloc"); }
+        h->pin_out.push_back(po);
         size_t nmax = 0;
         for (const auto& c : h->ch) nmax = std::max(nmax, (size_t)c.N * c.N);
         double* pin = nullptr;
@@ -753,7 +914,7 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     }
     cudaStream_t st = h->streams[j.slot];
     char* base = h->arena.base() + j.off;
-    void* ws = h->shared_ws ? h->shared_ws : base;
+    void* ws = h->shared_ws ? h->shared_ws : base;       // pipelined: chosen at launch
     const size_t fbytes = (size_t)b->F * ch.W * ch.H * (b->frame_type == SM_U16 ? 2 : 4);
     char* d_frames = h->shared_ws ? base : base + al(lay.bytes);
     j.d_out = reinterpret_cast<float*>(d_frames + al((size_t)b->F * ch.W * ch.H * 2 * 2));
@@ -794,6 +955,64 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     int rc = SM_OK;
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "staging burst");
+    } else if (h->mode == 2) {
+        std::lock_guard<std::mutex> lk(h->launch_mu);
+        const int w = (int)(h->n_launched++ & 1);
+        // stages before the bispectrum on the slot's high-priority stream
+        // (the spectra kernel takes whole SMs: it must not wait for phase
+        // CTAs), the bispectrum on the lowest, the back half in between (its
+        // CTAs are admitted first as the bispectrum's retire)
+        cudaStream_t ph = h->pstreams[j.slot], lo = h->lstreams[j.slot];
+        void* wsw = h->ws2[w];
+        if (h->front_recorded) e = cudaStreamWaitEvent(st, h->ev_front, 0);
+        if (e == cudaSuccess && h->free_recorded[w]) e = cudaStreamWaitEvent(st, h->ev_free[w], 0);
+        if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st);
+        if (e == cudaSuccess && !j.ev_mid) e = cudaEventCreateWithFlags(&j.ev_mid, cudaEventDisableTiming);
+        if (e == cudaSuccess && !j.ev_bis) e = cudaEventCreateWithFlags(&j.ev_bis, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "ordering burst");
+        } else {
+            if (j.d_seeing) j.d_seeing = at<double>(wsw, lay.seeing) + h->plans[b->channel]->dev.n_cubes;
+            rc = launch_burst(h, b, j, d_frames, est ? nullptr : d_stf, wsw, lay, st, 1, w);
+        }
+        if (rc == SM_OK) {
+            e = cudaEventRecord(j.ev_mid, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(lo, j.ev_mid, 0);
+            if (e != cudaSuccess) rc = cuda_fail(e, "ordering burst");
+        }
+        if (rc == SM_OK) rc = launch_burst(h, b, j, d_frames, est ? nullptr : d_stf, wsw, lay, lo, 3, w);
+        if (rc == SM_OK) {
+            e = cudaEventRecord(j.ev_bis, lo);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_front, lo);
+            h->front_recorded = e == cudaSuccess;
+            if (e != cudaSuccess) rc = cuda_fail(e, "ordering burst");
+        }
+        (void)ph;
+        // the previous burst's back half now goes after this burst's early
+        // stages; this burst's waits for the next burst (or its poll)
+        if (rc == SM_OK && h->pending_back) {
+            Job* pj = nullptr;
+            {
+                std::lock_guard<std::mutex> lk2(h->mu);
+                auto it = h->jobs.find(h->pending_back);
+                if (it != h->jobs.end() && it->second.back_pending) pj = &it->second;
+            }
+            h->pending_back = 0;
+            if (pj) {
+                const int brc = launch_back(h, *pj, j.ev_mid);
+                if (brc != SM_OK) pj->status = brc;
+            }
+        }
+        if (rc == SM_OK) {
+            j.back_pending = true;
+            j.bcopy = *b;
+            j.d_frames = d_frames;
+            j.d_stf = est ? nullptr : d_stf;
+            j.ws = wsw;
+            j.lay = lay;
+            j.wsi = w;
+            h->pending_back = j.ticket;
+        }
     } else {
         std::lock_guard<std::mutex> lk(h->launch_mu);
         if (!h->cfg.overlap_kernels && h->ordered) {
@@ -805,14 +1024,14 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
         }
         if (e != cudaSuccess) rc = cuda_fail(e, "ordering burst");
         else rc = launch_burst(h, b, j, d_frames, est ? nullptr : d_stf, ws, lay, st);
-        if (rc == SM_OK) {
-            e = cudaEventRecord(j.ev_done, st);
-            if (e == cudaSuccess && !h->cfg.overlap_kernels) {
-                e = cudaEventRecord(h->order, st);
-                h->ordered = e == cudaSuccess;
-            }
+        if (rc == SM_OK && !h->cfg.overlap_kernels) {
+            // the next burst's kernels need not wait for this one's copies
+            e = cudaEventRecord(h->order, st);
+            h->ordered = e == cudaSuccess;
             if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
         }
+        if (rc == SM_OK) rc = copy_back(h, j, ch, st);
+        if (rc == SM_OK) rc = ret(cudaEventRecord(j.ev_done, st), "cudaEventRecord");
     }
     std::lock_guard<std::mutex> lk(h->mu);
     if (rc != SM_OK) {
@@ -833,6 +1052,23 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
 extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result* res) {
     if (!h) { set_error("NULL handle"); return SM_EINVAL; }
     const auto start = Clock::now();
+    if (h->mode == 2) {
+        // a pipelined burst whose back half still waits for a next burst:
+        // the caller wants it now
+        std::lock_guard<std::mutex> lk0(h->launch_mu);
+        Job* pj = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(h->mu);
+            auto it = h->jobs.find(ticket);
+            if (it != h->jobs.end() && it->second.back_pending) pj = &it->second;
+        }
+        if (pj) {
+            if (h->pending_back == ticket) h->pending_back = 0;
+            DeviceGuard g(h->cfg.device);
+            const int brc = launch_back(h, *pj, nullptr);
+            if (brc != SM_OK) pj->status = brc;
+        }
+    }
     for (;;) {
         cudaEvent_t ev = nullptr;
         {
@@ -882,21 +1118,26 @@ extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result*
     DeviceGuard g(h->cfg.device);
     const sm_channel& ch = h->ch[j.channel];
     const size_t npx = (size_t)ch.W * ch.H;
-    cudaError_t e = cudaMemcpy(j.host_out, j.d_out, npx * sizeof(float), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && j.host_valid) e = cudaMemcpy(j.host_valid, j.d_valid, npx, cudaMemcpyDeviceToHost);
+    const char* pin = h->pin_out[j.slot];
+    if (j.staged) {            // the caller's buffers are pageable: from the pinned staging
+        std::memcpy(j.host_out, pin, npx * sizeof(float));
+        if (j.host_valid) std::memcpy(j.host_valid, pin + al(npx * 4), npx);
+    }
     double dr0 = 0.0;
-    if (e == cudaSuccess && j.d_seeing)
-        e = cudaMemcpy(&dr0, j.d_seeing_io ? j.d_seeing_io : j.d_seeing, sizeof(double), cudaMemcpyDeviceToHost);
+    if (j.d_seeing) std::memcpy(&dr0, pin + al(npx * 4) + al(npx), sizeof(double));
     float gms = 0.f;
     cudaEventElapsedTime(&gms, j.ev_start, j.ev_done);
     double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (j.marks)
-        for (size_t i = 0; i + 1 < j.marks->size(); ++i) {
+    for (int part = 0; part < 3; ++part) {
+        const std::vector<cudaEvent_t>* mk = part == 0 ? j.marks : part == 1 ? j.marks2 : j.marks3;
+        const std::vector<int>* ms_of = part == 0 ? j.mark_stage : part == 1 ? j.mark_stage2 : j.mark_stage3;
+        if (!mk) continue;
+        for (size_t i = 0; i + 1 < mk->size(); ++i) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, (*j.marks)[i], (*j.marks)[i + 1]) == cudaSuccess)
-                stage_ms[(*j.mark_stage)[i]] += ms;
+            if (cudaEventElapsedTime(&ms, (*mk)[i], (*mk)[i + 1]) == cudaSuccess) stage_ms[(*ms_of)[i]] += ms;
         }
-    int rc = e == cudaSuccess ? SM_OK : cuda_fail(e, "copying the mosaic");
+    }
+    int rc = SM_OK;
     if (res) {
         res->status = rc;
         res->t_submit_ms = j.t_submit;
@@ -925,9 +1166,16 @@ extern "C" int sm_close(sm_handle* h) {
         for (auto ev : kv.second.marks) cudaEventDestroy(ev);
     }
     h->graphs.clear();
+    for (auto s : h->pstreams) cudaStreamSynchronize(s);
+    for (auto s : h->lstreams) cudaStreamSynchronize(s);
     for (auto s : h->streams) cudaStreamDestroy(s);
+    for (auto s : h->pstreams) cudaStreamDestroy(s);
+    for (auto s : h->lstreams) cudaStreamDestroy(s);
     if (h->order) cudaEventDestroy(h->order);
+    if (h->ev_front) cudaEventDestroy(h->ev_front);
+    for (auto ev : h->ev_free) if (ev) cudaEventDestroy(ev);
     for (auto p : h->stf_pinned) cudaFreeHost(p);
+    for (auto p : h->pin_out) cudaFreeHost(p);
     if (h->dmem) {
         if (h->cfg.dev_free) h->cfg.dev_free(h->dmem, h->cfg.alloc_ctx);
         else cudaFree(h->dmem);

@@ -81,6 +81,36 @@ struct PlanDev {
     const double* t0;        // [hb_rows][box_pitch] diffraction OTF on the half box
 };
 
+constexpr int MAX_BATCH = 8;
+
+// One burst of a batched launch (k_batch.cu): its channel's plan, its frames
+// and the workspace buffers of all of its subfields (one chunk).
+struct BatchBurst {
+    PlanDev p;
+    const void* frames;
+    int frame_type, F;
+    void* spec;
+    float* flux;
+    float* mu;
+    float2* B;
+    int cnt_base;            // first of the burst's per-subfield dependency counters
+    int need;                // counter value a tile waits for: F when the launch
+                             //   transforms the frames, 0 when they were transformed before
+};
+// Buffers of the bursts of one plan in the batched tile grid.
+struct BatchPtrs {
+    const void* spec[MAX_BATCH];
+    float2* B[MAX_BATCH];
+    int F[MAX_BATCH];
+    int n;
+};
+// Kernel argument of the batched launch (passed by value, so a captured
+// graph holds it).
+struct BatchArgs {
+    BatchBurst b[MAX_BATCH];
+    int n;
+};
+
 }  // namespace smi
 
 // ---- kernel launchers (defined in the .cu files) ---------------------------
@@ -111,13 +141,19 @@ cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, in
 cudaError_t launch_refine(const smi::PlanDev& p, int nsub, const float2* B, const float* P, double2* z,
                           float2* partials, cudaStream_t st);
 cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M, const float* P,
-                         double2* z, cudaStream_t st);
+                         double2* z, cudaStream_t st, int threads = 512);
 cudaError_t launch_inverse(const smi::PlanDev& p, int F, int sub0, int nsub, const float* A,
                            const double2* z, const float* flux, const float* mu, float* rec,
                            cudaStream_t st);
 cudaError_t launch_mosaic(const smi::PlanDev& p, const float* rec, float* out, uint8_t* valid,
                           cudaStream_t st);
+cudaError_t launch_batch_grid(const smi::PlanDev& p, const smi::BatchPtrs& q, cudaStream_t st);
 size_t spectra_smem_bytes(int N, int K);
+size_t batch_smem_bytes(int N, int K, int prec);
+int batch_blocks_per_sm(size_t smem, int prec, int minb);
+cudaError_t launch_batch(const smi::BatchArgs& a, int prec, int minb, const int4* items, int n_items, int* head,
+                         int* cnt, int* status, float2* scratch, size_t scr_elems, int grid, size_t smem,
+                         cudaStream_t st);
 size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_ring_points,
                         int phase_prec);
 }  // namespace smk

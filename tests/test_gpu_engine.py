@@ -46,23 +46,27 @@ def _serve_one(eng, b, H, W):
     return out, valid.astype(bool)
 
 
-def test_engine_matches_plain_path(torch):
+@pytest.mark.parametrize("mode", [0, 2])
+def test_engine_matches_plain_path(torch, mode):
+    """Served in submission order or pipelined (the back half's 256-thread
+    phase kernel gives bitwise the phasors of the stage path's 512-thread
+    one), the mosaic is bitwise the plain stage path's."""
     from paper_1701_00581_gb300 import Engine
     ch = CS.gpu_channel("ragged")
     b = _bursts(1)[0]
     ref_out, ref_valid = _plain(torch, ch, b)
-    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2)
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2, overlap_kernels=mode)
     out, valid = _serve_one(eng, b, 110, 150)
     eng.close()
     assert np.array_equal(valid, ref_valid)
     assert np.array_equal(out, ref_out)
 
 
-@pytest.mark.parametrize("overlap", [False, True])
+@pytest.mark.parametrize("overlap", [0, 1, 2])
 def test_alone_equals_in_the_mix(torch, overlap):
     """Bursts admitted while others are on the device give the same mosaic
     (bitwise) as each burst served alone, with the bursts' kernels run in
-    submission order or concurrently."""
+    submission order, concurrently, or pipelined."""
     from paper_1701_00581_gb300 import Engine
     ch = CS.gpu_channel("ragged")
     bursts = _bursts(4)
@@ -140,14 +144,15 @@ def test_ordered_bursts_finish_in_submission_order(torch):
     eng.close()
 
 
-def test_stage_times(torch):
+@pytest.mark.parametrize("mode", [0, 2])
+def test_stage_times(torch, mode):
     """sm_result.stage_ms: every stage of the burst graph is timed; the
     seeing stage is empty when D/r0 is given and timed when estimated; the
     stages account for the burst's device time."""
     from paper_1701_00581_gb300 import STAGE_NAMES, Engine
     ch = CS.gpu_channel("ragged")
     b = _bursts(1)[0]
-    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2)
+    eng = Engine([ch], hbm_budget_bytes=1 << 30, max_inflight=2, overlap_kernels=mode)
     for given in (True, False):
         for _ in range(2):                    # first capture, then replay
             out = np.zeros((110, 150), np.float32)
@@ -330,3 +335,45 @@ def test_injected_allocation_failure_reports_on_its_ticket(torch, monkeypatch):
     for b, o in zip(bursts, outs):
         ref, _ = _plain(torch, ch, b)
         assert np.array_equal(o, ref)
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_results_reach_pinned_and_pageable_buffers(torch, mode):
+    """The mosaic and mask are copied back on the burst's own stream: into
+    page-locked caller buffers directly, into pageable ones through the
+    slot's pinned staging at poll time; both give the same result, and a
+    pipelined engine serves a second channel beside the first."""
+    from paper_1701_00581_gb300 import Channel, Engine
+    c0 = CS.gpu_channel("ragged")
+    c1 = Channel(W=96, H=80, N=64, R=6, stride=32, taper=8, max_frames=5)
+    b0 = _bursts(1)[0]
+    b1 = S.make_burst(S.BurstSpec(W=96, H=80, F=5, N=64, dr0=(4.0, 6.0), counts=True), channel=12)
+    eng = Engine([c0, c1], hbm_budget_bytes=1 << 30, max_inflight=3, overlap_kernels=mode)
+    pin_out = torch.zeros((110, 150), dtype=torch.float32).pin_memory()
+    pin_valid = torch.zeros((110, 150), dtype=torch.uint8).pin_memory()
+    page_out = np.zeros((110, 150), np.float32)
+    page_valid = np.zeros((110, 150), np.uint8)
+    o1 = np.zeros((80, 96), np.float32)
+    t_pin = eng.submit(0, b0["frames"], pin_out.numpy(), pin_valid.numpy(), d_over_r0=b0["d_over_r0"])
+    t_1 = eng.submit(1, b1["frames"], o1, d_over_r0=b1["d_over_r0"])
+    t_page = eng.submit(0, b0["frames"], page_out, page_valid, d_over_r0=b0["d_over_r0"])
+    for t in (t_page, t_1, t_pin):
+        assert eng.poll(t, -1)[0] == 0
+    eng.close()
+    ref, ref_valid = _plain(torch, c0, b0)
+    assert np.array_equal(pin_out.numpy(), ref) and np.array_equal(page_out, ref)
+    assert np.array_equal(pin_valid.numpy().astype(bool), ref_valid)
+    assert np.array_equal(page_valid.astype(bool), ref_valid)
+    plan1_out = _plain(torch, c1, b1)[0]
+    assert np.array_equal(o1, plan1_out)
+
+
+def test_pipelined_mode_needs_two_workspaces(torch):
+    from paper_1701_00581_gb300 import Channel, Engine, SpeckleError, _lib
+    ch = Channel(W=1024, H=1024, N=128, R=16, max_frames=100)
+    with pytest.raises(SpeckleError) as e:
+        Engine([ch], hbm_budget_bytes=4 << 30, max_inflight=2, overlap_kernels=2)
+    assert e.value.status == _lib.SM_ENOMEM
+    with pytest.raises(SpeckleError) as e:
+        Engine([ch], hbm_budget_bytes=4 << 30, max_inflight=2, overlap_kernels=3)
+    assert e.value.status == _lib.SM_EINVAL
