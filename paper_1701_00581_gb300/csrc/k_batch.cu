@@ -349,9 +349,11 @@ cudaError_t launch_batch_grid(const PlanDev& p, const smi::BatchPtrs& q, cudaStr
         if (vch) k_batch_grid<SM_FP32, true><<<grid, BT, 0, st>>>(p, q);
         else k_batch_grid<SM_FP32, false><<<grid, BT, 0, st>>>(p, q);
     } else if (p.prec == SM_FP16) {
-        k_batch_grid<SM_FP16, false><<<grid, BT, 0, st>>>(p, q);
+        if (vch) k_batch_grid<SM_FP16, true><<<grid, BT, 0, st>>>(p, q);
+        else k_batch_grid<SM_FP16, false><<<grid, BT, 0, st>>>(p, q);
     } else {
-        k_batch_grid<SM_BF16, false><<<grid, BT, 0, st>>>(p, q);
+        if (vch) k_batch_grid<SM_BF16, true><<<grid, BT, 0, st>>>(p, q);
+        else k_batch_grid<SM_BF16, false><<<grid, BT, 0, st>>>(p, q);
     }
     return cudaGetLastError();
 }

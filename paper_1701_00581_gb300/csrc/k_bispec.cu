@@ -16,8 +16,9 @@
 // (12 shared loads of 16 bytes for 32 pairs), so each triple product costs
 // 8 FP32 FMA-pipe instructions.
 //
-// FP32 spectra are staged by cp.async, four frames per barrier, while the
-// previous four frames are multiplied out.  W and U start at even box
+// Spectra are staged by cp.async, four frames per barrier, while the
+// previous four frames are multiplied out (half-precision spectra at half
+// the bytes, converted to FP32 once per stage in shared memory).  W and U start at even box
 // columns (the plan places the offset grid so that they do), so they move in
 // 16-byte copies of two spectrum values, and so does V when the box's
 // centre column K is odd: 212 copies per frame, two per thread (otherwise V
@@ -54,17 +55,21 @@ cudaError_t launch_bispectrum(const smi::PlanDev& p, const void* spec, int F, in
             if (vch) k_bispectrum<SM_FP32, true, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
             else k_bispectrum<SM_FP32, false, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
         } else if (p.prec == SM_FP16) {
-            k_bispectrum<SM_FP16, false, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+            if (vch) k_bispectrum<SM_FP16, true, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+            else k_bispectrum<SM_FP16, false, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
         } else {
-            k_bispectrum<SM_BF16, false, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+            if (vch) k_bispectrum<SM_BF16, true, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+            else k_bispectrum<SM_BF16, false, true><<<grid, THREADS, 0, st>>>(p, spec, F, B);
         }
     } else if (p.prec == SM_FP32) {
         if (vch) k_bispectrum<SM_FP32, true, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
         else k_bispectrum<SM_FP32, false, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
     } else if (p.prec == SM_FP16) {
-        k_bispectrum<SM_FP16, false, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        if (vch) k_bispectrum<SM_FP16, true, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        else k_bispectrum<SM_FP16, false, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
     } else {
-        k_bispectrum<SM_BF16, false, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        if (vch) k_bispectrum<SM_BF16, true, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
+        else k_bispectrum<SM_BF16, false, false><<<grid, THREADS, 0, st>>>(p, spec, F, B);
     }
     return cudaGetLastError();
 }

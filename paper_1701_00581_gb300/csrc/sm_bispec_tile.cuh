@@ -2,6 +2,8 @@
 // shared by the per-stage kernel (k_bispec.cu) and the batched persistent
 // launch (k_batch.cu).
 #pragma once
+#include <type_traits>
+
 #include "sm_internal.h"
 
 namespace smb {
@@ -25,9 +27,8 @@ constexpr int OFF_W = 0;
 constexpr int OFF_V = smi::WBY * PW;                      // 144
 constexpr int OFF_U = OFF_V + smi::VBY * smi::VBX;        // 176
 constexpr int BUF = OFF_U + UR * PU;                      // 462 float2 per frame buffer
-constexpr int NLOAD = smi::WBY * smi::WBX + smi::VBY * smi::VBX + UR * UC;  // 413 values
+constexpr int NLOAD = smi::WBY * smi::WBX + smi::VBY * smi::VBX + UR * UC;  // 413 values staged per frame
 constexpr int THREADS = smi::BISPEC_THREADS;
-constexpr int LPT = (NLOAD + THREADS - 1) / THREADS;      // 4 values per thread (half precision)
 static_assert(OFF_V % 2 == 0 && OFF_U % 2 == 0 && BUF % 2 == 0 && PW % 2 == 0 && PU % 2 == 0,
               "16-byte shared accesses need even float2 offsets");
 
@@ -51,20 +52,6 @@ static_assert(smi::WBX % 2 == 0, "targets start at even box columns");
 // mod 8, distinct.  Differences: slot 13 row + 2 gx + q, rows of lanes 0..7
 // differ by 1 -> {0,2,4,6} + {0,5} mod 8, distinct.  Offsets: broadcast.
 
-template <int PREC>
-__device__ __forceinline__ float2 load_spec(const void* spec, size_t idx) {
-    if (PREC == SM_FP32) {
-        return __ldg(reinterpret_cast<const float2*>(spec) + idx);
-    } else if (PREC == SM_FP16) {
-        const __half2 h = reinterpret_cast<const __half2*>(spec)[idx];
-        const float2 v = __half22float2(h);
-        return make_float2(v.x * smi::FP16_INV_SCALE, v.y * smi::FP16_INV_SCALE);
-    } else {
-        const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162*>(spec)[idx];
-        return __bfloat1622float2(h);
-    }
-}
-
 __device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2i, int R2) {
     const int w2 = wx * wx + wy * wy, v2 = vx * vx + vy * vy;
     const int ux = wx - vx, uy = wy - vy, u2 = ux * ux + uy * uy;
@@ -79,6 +66,16 @@ __device__ __forceinline__ void cp_async8(unsigned smem_addr, const void* gmem, 
 }
 __device__ __forceinline__ void cp_async16(unsigned smem_addr, const void* gmem, int bytes) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" :: "r"(smem_addr), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async4(unsigned smem_addr, const void* gmem, int bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(smem_addr), "l"(gmem), "r"(bytes));
+}
+// Chunk copies of E-byte spectrum values: two values (2E bytes) or one (E).
+template <int E> __device__ __forceinline__ void cp_pair(unsigned s, const void* g, int bytes) {
+    if (E == 8) cp_async16(s, g, bytes); else cp_async8(s, g, bytes);
+}
+template <int E> __device__ __forceinline__ void cp_one(unsigned s, const void* g, int bytes) {
+    if (E == 8) cp_async8(s, g, bytes); else cp_async4(s, g, bytes);
 }
 
 // acc += t with Kahan compensation (c carries the rounding error of the sum);
@@ -138,14 +135,28 @@ __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, 
     }
 }
 
-// Staging: FP32 spectra go straight from global to shared memory by cp.async
-// (zero-filled outside the box), FB frames per stage in a two-stage ring, so
-// one barrier serves FB frames; half-precision spectra are converted in
-// registers one frame ahead.
+// Staging: spectra go from global to shared memory by cp.async (zero-filled
+// outside the box), FB frames per stage in a two-stage ring, so one barrier
+// serves FB frames.  FP32 values (E = 8 bytes) are multiplied out from the
+// ring itself.  Half-precision values (E = 4: half2 or bfloat162) are
+// copied raw, at half the bytes, and converted to FP32 once per stage into a
+// compute buffer (a second barrier per stage), so the inner loop is the same
+// as for FP32.  The ring and the compute buffer of the half-precision path
+// fill the same 2 FB BUF float2 of shared memory as the FP32 ring.
 template <int PREC> struct Staging;
-template <> struct Staging<SM_FP32> { static constexpr bool ASYNC = true;  static constexpr int FB = 4; };
-template <> struct Staging<SM_FP16> { static constexpr bool ASYNC = false; static constexpr int FB = 1; };
-template <> struct Staging<SM_BF16> { static constexpr bool ASYNC = false; static constexpr int FB = 1; };
+template <> struct Staging<SM_FP32> { static constexpr bool ASYNC = true; static constexpr int FB = 4, E = 8; };
+template <> struct Staging<SM_FP16> { static constexpr bool ASYNC = true; static constexpr int FB = 4, E = 4; };
+template <> struct Staging<SM_BF16> { static constexpr bool ASYNC = true; static constexpr int FB = 4, E = 4; };
+
+template <int PREC>
+__device__ __forceinline__ float2 raw_to_float2(unsigned w) {
+    if (PREC == SM_FP16) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
+        return make_float2(v.x * smi::FP16_INV_SCALE, v.y * smi::FP16_INV_SCALE);
+    } else {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    }
+}
 
 // Box index of spectrum value (kx, ky), or -1 outside the stored box.
 __device__ __forceinline__ int box_index(const PlanDev& p, int kx, int ky) {
@@ -187,7 +198,8 @@ template <int PREC, bool VCH, bool KAHAN>
 __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __restrict__ spec, int F,
                                             float2* __restrict__ B, int tile, int sl, float2* __restrict__ S) {
     constexpr bool ASYNC = Staging<PREC>::ASYNC;
-    constexpr int FB = Staging<PREC>::FB;
+    constexpr int FB = Staging<PREC>::FB, E = Staging<PREC>::E;
+    constexpr bool RAW = E == 4;                  // half precision: raw ring + FP32 compute buffer
     const int4 T = p.tiles[tile];
     const int wx0 = T.x, wy0 = T.y, vx0 = T.z, vy0 = T.w;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -224,48 +236,55 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
         }
     };
     if (ASYNC) {
-        const float2* sp = reinterpret_cast<const float2*>(spec) + sbase;
+        // spectrum values as E-byte words: float2, or half2 / bfloat162
+        using Word = typename std::conditional<E == 8, float2, unsigned>::type;
+        const Word* sp = reinterpret_cast<const Word*>(spec) + sbase;
         const int nst = (F + FB - 1) / FB;
+        // The ring: E-byte slots, 2 stages x FB frames x BUF; the half-
+        // precision compute buffer (FB x BUF float2) follows it.
+        Word* ring = reinterpret_cast<Word*>(S);
+        float2* cbuf = S + FB * BUF;
         // Copy slots, fixed for the CTA: global source at frame 0, shared
-        // destination in buffer 0 and size.
+        // destination in buffer 0 and size (chunk_copy counts 8-byte values).
         int src, dst, nb0, nb1 = 0;
         chunk_copy<VCH>(p, tid, wx0, wy0, vx0, vy0, src, dst, nb0);
-        const float2* g0 = sp + src;
-        const unsigned s0 = (unsigned)__cvta_generic_to_shared(S + dst);
-        const bool v8 = !VCH && warp == 0;                  // warp 0 copies V by 8 bytes
+        nb0 = nb0 * E / 8;
+        const Word* g0 = sp + src;
+        const unsigned s0 = (unsigned)__cvta_generic_to_shared(ring + dst);
+        const bool v8 = !VCH && warp == 0;                  // warp 0 copies V by single values
         const int c1 = VCH ? tid + THREADS : tid + THREADS - NV;
         const bool has1 = v8 || c1 < NCH_W + NCH_U + (VCH ? NCH_V : 0);
         if (v8) {
             const int r = lane >> 3, c = lane & 7;
             const int i = box_index(p, vx0 + c, vy0 + r);
-            src = i >= 0 ? i : 0; dst = OFF_V + r * smi::VBX + c; nb1 = i >= 0 ? 8 : 0;
+            src = i >= 0 ? i : 0; dst = OFF_V + r * smi::VBX + c; nb1 = i >= 0 ? E : 0;
         } else if (has1) {
             chunk_copy<VCH>(p, c1, wx0, wy0, vx0, vy0, src, dst, nb1);
+            nb1 = nb1 * E / 8;
         } else {
             src = 0; dst = 0;
         }
-        const float2* g1 = sp + src;
-        const unsigned s1 = (unsigned)__cvta_generic_to_shared(S + dst);
+        const Word* g1 = sp + src;
+        const unsigned s1 = (unsigned)__cvta_generic_to_shared(ring + dst);
         auto copy = [&](unsigned soff, size_t goff, int n0, int n1) {
-            cp_async16(s0 + soff, g0 + goff, n0);
-            if (v8) cp_async8(s1 + soff, g1 + goff, n1);
-            else if (has1) cp_async16(s1 + soff, g1 + goff, n1);
+            cp_pair<E>(s0 + soff, g0 + goff, n0);
+            if (v8) cp_one<E>(s1 + soff, g1 + goff, n1);
+            else if (has1) cp_pair<E>(s1 + soff, g1 + goff, n1);
         };
         // Stage st holds frames FB st .. FB st + FB - 1; frames past F are
         // zero-filled (no global read) so that every stage is multiplied out whole.
         auto issue = [&](int st) {
             if (st < nst) {
-                const unsigned sb = (unsigned)((st & 1) * FB * BUF * sizeof(float2));
+                const unsigned sb = (unsigned)((st & 1) * FB * BUF * E);
                 if (st * FB + FB <= F) {
 #pragma unroll
                     for (int ff = 0; ff < FB; ++ff)
-                        copy(sb + ff * BUF * sizeof(float2), (size_t)(st * FB + ff) * box, nb0, nb1);
+                        copy(sb + ff * BUF * E, (size_t)(st * FB + ff) * box, nb0, nb1);
                 } else {
 #pragma unroll
                     for (int ff = 0; ff < FB; ++ff) {
                         const bool in = st * FB + ff < F;
-                        copy(sb + ff * BUF * sizeof(float2), in ? (size_t)(st * FB + ff) * box : 0,
-                             in ? nb0 : 0, in ? nb1 : 0);
+                        copy(sb + ff * BUF * E, in ? (size_t)(st * FB + ff) * box : 0, in ? nb0 : 0, in ? nb1 : 0);
                     }
                 }
             }
@@ -290,8 +309,17 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
                 asm volatile("cp.async.wait_group 0;");
                 __syncthreads();          // stage st visible to all; stage st-1 fully consumed
                 issue(st + 1);
+                const float2* Sst;
+                if constexpr (RAW) {
+                    // the stage's values to FP32, once, for every warp
+                    const unsigned* rs = reinterpret_cast<const unsigned*>(ring) + (st & 1) * FB * BUF;
+                    for (int e = tid; e < FB * BUF; e += THREADS) cbuf[e] = raw_to_float2<PREC>(rs[e]);
+                    __syncthreads();
+                    Sst = cbuf;
+                } else {
+                    Sst = reinterpret_cast<const float2*>(ring) + (st & 1) * FB * BUF;
+                }
                 if (!pm) continue;
-                const float2* Sst = S + (st & 1) * FB * BUF;
                 if (pm == (1u << NC) - 1u) {
 #pragma unroll
                     for (int ff = 0; ff < FB; ++ff)
@@ -303,63 +331,6 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
                 }
             }
             asm volatile("cp.async.wait_group 0;");
-            if (pm) write_out(col0, acc);
-        }
-    } else {
-        // Which spectrum value each thread stages, and where it goes.
-        int src[LPT], dst[LPT];
-#pragma unroll
-        for (int i = 0; i < LPT; ++i) {
-            const int e = tid + i * THREADS;
-            int d = -1, s = -1;
-            if (e < smi::WBY * smi::WBX) {
-                const int r = e / smi::WBX, c = e - r * smi::WBX;
-                s = box_index(p, wx0 + c, wy0 + r); d = OFF_W + r * PW + c;
-            } else if (e < smi::WBY * smi::WBX + smi::VBY * smi::VBX) {
-                const int e2 = e - smi::WBY * smi::WBX;
-                const int r = e2 / smi::VBX, c = e2 - r * smi::VBX;
-                s = box_index(p, vx0 + c, vy0 + r); d = OFF_V + r * smi::VBX + c;
-            } else if (e < NLOAD) {
-                const int e2 = e - smi::WBY * smi::WBX - smi::VBY * smi::VBX;
-                const int r = e2 / UC, c = e2 - r * UC;
-                s = box_index(p, wx0 - vx0 - (smi::VBX - 1) + c, wy0 - vy0 - (smi::VBY - 1) + r);
-                d = OFF_U + r * PU + c;
-            }
-            dst[i] = d;
-            src[i] = s;
-        }
-#pragma unroll
-        for (int pass = 0; pass < NP; ++pass) {
-            const int col0 = pass * NC;
-            const unsigned pm = (kkmask >> col0) & ((1u << NC) - 1u);
-            float2 acc[4][NC];
-            float2 comp[4][KAHAN ? NC : 1];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                for (int k = 0; k < NC; ++k) acc[j][k] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int k = 0; k < (KAHAN ? NC : 1); ++k) comp[j][k] = make_float2(0.f, 0.f);
-            }
-            if (pass > 0) __syncthreads();             // the previous pass is done with the buffers
-            float2 pre[LPT];
-#pragma unroll
-            for (int i = 0; i < LPT; ++i)
-                pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, sbase + src[i]) : make_float2(0.f, 0.f);
-            for (int f = 0; f < F; ++f) {
-                float2* Sb = S + (f & 1) * BUF;
-#pragma unroll
-                for (int i = 0; i < LPT; ++i)
-                    if (dst[i] >= 0) Sb[dst[i]] = pre[i];
-                __syncthreads();
-                if (f + 1 < F) {
-                    const size_t fb = sbase + (size_t)(f + 1) * box;
-#pragma unroll
-                    for (int i = 0; i < LPT; ++i)
-                        pre[i] = src[i] >= 0 ? load_spec<PREC>(spec, fb + src[i]) : make_float2(0.f, 0.f);
-                }
-                if (pm) accumulate_frame<false, NC, KAHAN>(Sb, wyl, gx, warp, pm, col0, acc, comp);
-            }
             if (pm) write_out(col0, acc);
         }
     }
