@@ -436,7 +436,13 @@ typedef struct {
                                            bispectrum (the recursion takes a
                                            quarter of an SM and fills the
                                            issue slots the ALU-bound
-                                           bispectrum leaves)                 */
+                                           bispectrum leaves);
+                                           3: batched -- bursts submitted
+                                           together (sm_submit_batch) run
+                                           through one batched launch
+                                           (sm_batch_*), batches in
+                                           submission order; every burst
+                                           holds a whole-burst workspace     */
     /* Optional device allocator for the engine's one arena of
      * hbm_budget_bytes (both NULL: cudaMalloc / cudaFree).  dev_alloc is
      * called once by sm_open and must return device memory of `device`
@@ -512,6 +518,16 @@ int sm_open(const sm_config* cfg, sm_handle** out);
  * burst gets a ticket, nothing is queued, and sm_poll reports SM_ENOMEM for
  * it; the engine stays usable (a host-side failure injection for tests).   */
 int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket);
+/* sm_submit_batch: stage n bursts (1..8, of any of the engine's channels)
+ * and queue them as one batch: their transforms and bispectra in one batched
+ * launch, then each burst's remaining stages (sm_batch_reconstruct, with the
+ * autotuned launch shape), captured once per batch composition and arena
+ * placement as a CUDA graph.  Needs an engine opened with
+ * overlap_kernels = 3.  tickets: [n], one per burst, polled as usual
+ * (stage_ms is not split for batched bursts).  All-or-nothing: SM_EBUSY
+ * when the slots or the budget cannot take the whole batch now.            */
+int sm_submit_batch(sm_handle* h, int n, const sm_burst* b, uint64_t* tickets);
+
 /* sm_poll: the mosaic of one burst (Sect. 3.2: the merged image) -- wait
  * up to timeout_ms (0 = test and return SM_PENDING, > 0 = return SM_ETIMEDOUT
  * when it elapses, < 0 = forever).  SM_OK once the mosaic (and mask) are in

@@ -310,7 +310,8 @@ class Engine:
                  device: int = 0, overlap_kernels: int = 0, allocator: Optional[str] = None):
         """``overlap_kernels``: 0 the bursts' kernels in submission order, 1
         concurrently, 2 pipelined (a burst's phase, inverse and mosaic beside
-        the next burst's transforms and bispectrum).  ``allocator="torch"``
+        the next burst's transforms and bispectrum), 3 batched (bursts
+        submitted together run through one batched launch).  ``allocator="torch"``
         takes the engine's arena from torch's caching allocator (one uint8
         tensor held until close) instead of cudaMalloc."""
         self.lib = load()
@@ -359,6 +360,38 @@ class Engine:
         check(self.lib.sm_submit_burst(self.h, C.byref(b), C.byref(t)), "sm_submit_burst")
         self._keep[t.value] = (out, valid)
         return t.value
+
+    def submit_batch(self, bursts) -> list:
+        """sm_submit_batch (engine opened with overlap_kernels=3): ``bursts`` is
+        a list of dicts with channel, frames, out and optionally valid, stf,
+        d_over_r0; returns one ticket per burst, or raises SpeckleError
+        (SM_EBUSY when the whole batch cannot be admitted now)."""
+        n = len(bursts)
+        arr = (_lib.sm_burst * n)()
+        keep = []
+        for i, d in enumerate(bursts):
+            frames = d["frames"]
+            on_dev = not isinstance(frames, np.ndarray)
+            ft = SM_U16 if str(frames.dtype).endswith("uint16") else SM_F32
+            stf = None if d.get("stf") is None else np.ascontiguousarray(d["stf"], dtype=np.float64)
+            dr0 = None if d.get("d_over_r0") is None else np.ascontiguousarray(d["d_over_r0"], dtype=np.float64)
+            keep.append((stf, dr0))
+            arr[i] = _lib.sm_burst(d["channel"], frames.shape[0], _ptr(frames), ft, 1 if on_dev else 0, _ptr(stf),
+                                   _ptr(dr0), _ptr(d["out"]), _ptr(d.get("valid")))
+        t = (C.c_uint64 * n)()
+        check(self.lib.sm_submit_batch(self.h, n, arr, t), "sm_submit_batch")
+        tickets = list(t)
+        for tk, d in zip(tickets, bursts):
+            self._keep[tk] = (d["out"], d.get("valid"))
+        return tickets
+
+    def try_submit_batch(self, bursts) -> Optional[list]:
+        try:
+            return self.submit_batch(bursts)
+        except SpeckleError as e:
+            if e.status == _lib.SM_EBUSY:
+                return None
+            raise
 
     def try_submit(self, *args, **kw) -> Optional[int]:
         try:

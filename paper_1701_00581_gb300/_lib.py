@@ -118,6 +118,7 @@ SIGNATURES = {
     "sm_batch_status": (_I, [_P]),
     "sm_open": (_I, [C.POINTER(sm_config), C.POINTER(_P)]),
     "sm_submit_burst": (_I, [_P, C.POINTER(sm_burst), C.POINTER(C.c_uint64)]),
+    "sm_submit_batch": (_I, [_P, _I, C.POINTER(sm_burst), C.POINTER(C.c_uint64)]),
     "sm_poll": (_I, [_P, C.c_uint64, _I, C.POINTER(sm_result)]),
     "sm_close": (_I, [_P]),
     "sm_strerror": (C.c_char_p, [_I]),

@@ -100,12 +100,27 @@ k_spectra(PlanDev p, const TIn* __restrict__ frames, int F, int sub0, void* __re
     float* swy = swx + N;
     double* red = reinterpret_cast<double*>(swy + N);
 
-    const int f = blockIdx.x, sl = blockIdx.y, s = sub0 + sl;
+    // frame-major grid: consecutive CTAs cut neighbouring subfields of one
+    // frame, whose tiles overlap, so most tile reads hit L2
+    const int sl = blockIdx.x, f = blockIdx.y, s = sub0 + sl;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int grp = tid / G, g = tid - grp * G;
     float2* T = scratch + grp * TB;
     const int4 sb = p.subs[s];
     const int x0 = sb.x, y0 = sb.y, w = sb.z, h = sb.w;
+    {
+        // the whole tile towards L2 now, so the row rounds after the first
+        // do not wait on DRAM: one prefetch per 128-byte line of each row
+        const char* fb = reinterpret_cast<const char*>(frames + (size_t)f * p.H * p.W + (size_t)y0 * p.W);
+        const size_t b0 = (size_t)x0 * sizeof(TIn), b1 = (size_t)(x0 + w) * sizeof(TIn);
+        const int l0 = (int)(b0 >> 7), nl = (int)(((b1 - 1) >> 7) - (b0 >> 7)) + 1;
+        for (int e = tid; e < h * nl; e += TS) {
+            const int y = e / nl, l = e - y * nl;
+            const size_t off = (size_t)y * p.W * sizeof(TIn) + ((size_t)(l0 + l) << 7);
+            const size_t lo = (size_t)y * p.W * sizeof(TIn) + b0;   // stay inside the tile's row
+            asm volatile("prefetch.global.L2 [%0];" :: "l"(fb + (off > lo ? off : lo)));
+        }
+    }
     for (int i = tid; i < N; i += TS) {
         stw[i] = p.tw[i];
         swx[i] = p.winx[(size_t)s * N + i];
@@ -321,7 +336,7 @@ template <int N>
 cudaError_t spectra_n(const PlanDev& p, const void* frames, int frame_type, int F, int sub0,
                       int nsub, void* spec, float* flux, float* mu, cudaStream_t st) {
     const size_t sm = fft_smem(N, p.K);
-    dim3 grid(F, nsub);
+    dim3 grid(nsub, F);
     cudaError_t e = cudaSuccess;
 #define SM_LAUNCH(TIN, PREC)                                                                    \
     do {                                                                                        \

@@ -195,13 +195,10 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
         const int npn = more ? p.ring_start[r + 2] - p.ring_start[r + 1] : 0;
         stage(r + 1);
         // (1) items: products in T, one term per lane, item sums in T
-        for (int job = 0, vw = warp, base = warp; vw < PH_VWARPS; ++job) {
-            if (base >= ni) {                    // this virtual warp is done: the next one
-                vw += PH_WARPS;
-                base = vw;
-                continue;
-            }
-            if (job != 0) load_batch(p.items + i0, base, ni);
+        // One batch of up to PH_ITEMS items of a (virtual) warp: 512 threads
+        // give one virtual warp per warp, 256 two, one after the other.
+        auto item_batch = [&](int base, bool first) {
+            if (!first) load_batch(p.items + i0, base, ni);
             T2 t[PH_ITEMS];
 #pragma unroll
             for (int q = 0; q < PH_ITEMS; ++q) {
@@ -239,7 +236,16 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
             const T2 sum = reduce8(t, lane);
             const int e = base + (lane >> 2) * PH_VWARPS;
             if ((lane & 3) == 0 && e < ni) part[e] = sum;
-            base += PH_VWARPS * PH_ITEMS;
+        };
+        if constexpr (TH == 512) {
+            for (int base = warp; base < ni; base += PH_VWARPS * PH_ITEMS) item_batch(base, base == warp);
+        } else {
+            bool first = true;
+            for (int vw = warp; vw < PH_VWARPS; vw += PH_WARPS)
+                for (int base = vw; base < ni; base += PH_VWARPS * PH_ITEMS) {
+                    item_batch(base, first);
+                    first = false;
+                }
         }
         asm volatile("cp.async.wait_group 0;");
         __syncthreads();                          // partials complete, ring r+1 records visible

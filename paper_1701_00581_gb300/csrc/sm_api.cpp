@@ -476,6 +476,7 @@ struct Job {
     sm_workspace_layout lay{};
     int wsi = 0;
     bool staged = false;                  // the mosaic went to the slot's pinned staging, not to out
+    const sm_batch* batch = nullptr;      // batched mode: the batch object the burst ran in
     double t_submit = 0.0;
     int status = SM_PENDING;
 };
@@ -506,6 +507,7 @@ struct sm_handle {
         std::vector<int> stage;           // reported stage of each call
     };
     std::map<std::tuple<int, int, size_t, int>, Graph> graphs;
+    std::map<std::vector<size_t>, Graph> bgraphs;     // batched mode: by composition and placement
     // Device order of the bursts' kernels (overlap_kernels == 0): re-recorded
     // on the launching stream after every burst, and waited on by the next
     // burst's stream before its graph, under launch_mu so that the wait,
@@ -532,6 +534,9 @@ struct sm_handle {
     bool front_recorded = false, free_recorded[2] = {false, false};
     uint64_t n_launched = 0;
     uint64_t pending_back = 0;            // ticket whose back half waits for the next burst (0: none)
+    // Batched (overlap_kernels = 3): one batch object per composition
+    // (channel, F, frame type of each burst, in order).
+    std::map<std::vector<int>, sm_batch*> batches;
     std::vector<cudaStream_t> pstreams;   // per slot, middle priority (pipelined back halves)
     std::vector<cudaStream_t> lstreams;   // per slot, lowest priority (pipelined bispectra)
     // Per slot: pinned staging for the mosaic, mask and seeing value, copied
@@ -745,14 +750,14 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
     // largest count that does.  Concurrent kernels: each burst's workspace
     // and buffers in an equal share of the budget.  In order: one shared
     // workspace beside max_inflight bursts' own buffers.
-    if (cfg->overlap_kernels < 0 || cfg->overlap_kernels > 2) {
+    if (cfg->overlap_kernels < 0 || cfg->overlap_kernels > 3) {
         for (auto* q : h->plans) sm_plan_destroy(q);
         delete h;
-        set_error("overlap_kernels must be 0, 1 or 2");
+        set_error("overlap_kernels must be 0, 1, 2 or 3");
         return SM_EINVAL;
     }
     h->mode = cfg->overlap_kernels;
-    const bool shared = h->mode != 1;
+    const bool shared = h->mode == 0 || h->mode == 2;
     size_t io_max = 0;
     for (int c = 0; c < cfg->n_channels; ++c) io_max = std::max(io_max, io_bytes(h, c, h->ch[c].max_frames));
     const size_t io_all = io_max * (size_t)cfg->max_inflight;
@@ -774,7 +779,16 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
             if (fits(mid)) lo = mid; else hi = mid - 1;
         }
         h->chunk[c] = lo;
-        if (h->mode == 2) {
+        if (h->mode == 3) {
+            // a batched burst holds every subfield's workspace (one chunk)
+            h->chunk[c] = p->dev.n_sub;
+            if (burst_bytes(h, c, h->ch[c].max_frames, &lay) > cfg->hbm_budget_bytes) {
+                for (auto* q : h->plans) sm_plan_destroy(q);
+                delete h;
+                set_error("batched mode: hbm_budget_bytes cannot hold one whole burst");
+                return SM_ENOMEM;
+            }
+        } else if (h->mode == 2) {
             // two unchunked workspaces (a burst's back half reads its whole
             // workspace while the next burst's front half fills the other)
             h->chunk[c] = p->dev.n_sub;
@@ -862,6 +876,7 @@ extern "C" int sm_open(const sm_config* cfg, sm_handle** out) {
 
 extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket) {
     if (!h || !b || !ticket) { set_error("NULL argument"); return SM_EINVAL; }
+    if (h->mode == 3) return sm_submit_batch(h, 1, b, ticket);
     if (b->channel < 0 || b->channel >= (int)h->ch.size()) { set_error("bad channel"); return SM_EINVAL; }
     const sm_channel& ch = h->ch[b->channel];
     if (b->F < 1 || b->F > ch.max_frames || !b->frames || !b->out) { set_error("bad burst"); return SM_EINVAL; }
@@ -1049,6 +1064,187 @@ extern "C" int sm_submit_burst(sm_handle* h, const sm_burst* b, uint64_t* ticket
     return SM_OK;
 }
 
+// Batched mode: n bursts staged together and run as one batch.  Staging is
+// the per-burst staging of sm_submit_burst (own slot stream, frames and STF
+// copied in, the caller's buffers free on return); the batch then runs on
+// the first burst's stream after every burst's copies, in submission order.
+extern "C" int sm_submit_batch(sm_handle* h, int n, const sm_burst* bs, uint64_t* tickets) {
+    if (!h || !bs || !tickets) { set_error("NULL argument"); return SM_EINVAL; }
+    if (h->mode != 3) { set_error("sm_submit_batch needs an engine opened with overlap_kernels = 3"); return SM_EINVAL; }
+    if (n < 1 || n > MAX_BATCH) { set_error("a batch holds 1..8 bursts"); return SM_EINVAL; }
+    std::vector<sm_workspace_layout> lays(n);
+    std::vector<size_t> need(n);
+    std::vector<std::vector<double>> stfs(n);
+    for (int i = 0; i < n; ++i) {
+        const sm_burst* b = bs + i;
+        if (b->channel < 0 || b->channel >= (int)h->ch.size()) { set_error("bad channel"); return SM_EINVAL; }
+        const sm_channel& ch = h->ch[b->channel];
+        if (b->F < 1 || b->F > ch.max_frames || !b->frames || !b->out) { set_error("bad burst"); return SM_EINVAL; }
+        if (b->frame_type != SM_U16 && b->frame_type != SM_F32) { set_error("bad frame_type"); return SM_EINVAL; }
+        const bool est = !b->stf && !b->d_over_r0;
+        if (est && (h->plans[b->channel]->dev.n_cubes < 1 || b->F < 2)) {
+            set_error("no stf or d_over_r0, and the seeing cannot be estimated (needs a cube and F >= 2)");
+            return SM_EINVAL;
+        }
+        if (!b->stf && !est) {
+            stfs[i].resize((size_t)ch.N * ch.N);
+            int rc = sm_model_stf(&ch, b->F, b->d_over_r0, stfs[i].data());
+            if (rc) return rc;
+        }
+        need[i] = burst_bytes(h, b->channel, b->F, &lays[i]);
+        if (need[i] > h->arena_bytes) { set_error("burst exceeds the HBM budget"); return SM_ENOMEM; }
+    }
+    DeviceGuard g(h->cfg.device);
+    std::vector<Job> js(n);
+    {
+        // all or nothing: n slots and n arena blocks, or none
+        std::lock_guard<std::mutex> lk(h->mu);
+        std::vector<int> slots;
+        for (size_t i = 0; i < h->streams.size() && (int)slots.size() < n; ++i)
+            if (!h->stream_busy[i]) slots.push_back((int)i);
+        if ((int)slots.size() < n) { set_error("not enough free in-flight slots for the batch"); return SM_EBUSY; }
+        std::vector<size_t> offs;
+        for (int i = 0; i < n; ++i) {
+            size_t off = 0;
+            if (!h->arena.alloc(need[i], &off)) {
+                for (int k = 0; k < i; ++k) h->arena.release(offs[k], need[k]);
+                set_error("budget full");
+                return SM_EBUSY;
+            }
+            offs.push_back(off);
+        }
+        for (int i = 0; i < n; ++i) {
+            h->stream_busy[slots[i]] = true;
+            js[i].slot = slots[i];
+            js[i].off = offs[i];
+            js[i].bytes = need[i];
+            js[i].ticket = h->next_ticket++;
+        }
+    }
+    std::vector<sm_batch_io> io(n);
+    std::vector<const sm_plan*> plans(n);
+    std::vector<int> Fs(n), fts(n), key;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const sm_burst* b = bs + i;
+        const sm_channel& ch = h->ch[b->channel];
+        Job& j = js[i];
+        cudaStream_t st = h->streams[j.slot];
+        char* base = h->arena.base() + j.off;
+        void* ws = base;
+        char* d_frames = base + al(lays[i].bytes);
+        const size_t fbytes = (size_t)b->F * ch.W * ch.H * (b->frame_type == SM_U16 ? 2 : 4);
+        j.d_out = reinterpret_cast<float*>(d_frames + al((size_t)b->F * ch.W * ch.H * 2 * 2));
+        j.d_valid = reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(j.d_out) + al((size_t)ch.W * ch.H * 4));
+        double* d_stf = reinterpret_cast<double*>(reinterpret_cast<char*>(j.d_valid) + al((size_t)ch.W * ch.H));
+        const bool est = !b->stf && !b->d_over_r0;
+        j.channel = b->channel;
+        j.F = b->F;
+        if (est) j.d_seeing = at<double>(ws, lays[i].seeing) + h->plans[b->channel]->dev.n_cubes;
+        j.host_out = b->out;
+        j.host_valid = b->valid;
+        e = cudaEventCreate(&j.ev_start);
+        if (e == cudaSuccess) e = cudaEventCreate(&j.ev_done);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_frames, b->frames, fbytes,
+                                b->frames_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !est) {
+            double* pin = h->stf_pinned[j.slot];
+            std::memcpy(pin, b->stf ? b->stf : stfs[i].data(), (size_t)ch.N * ch.N * sizeof(double));
+            e = cudaMemcpyAsync(d_stf, pin, (size_t)ch.N * ch.N * sizeof(double), cudaMemcpyHostToDevice, st);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st);
+        io[i] = sm_batch_io{d_frames, est ? nullptr : d_stf, ws, nullptr, j.d_out, j.d_valid};
+        plans[i] = h->plans[b->channel];
+        Fs[i] = b->F;
+        fts[i] = b->frame_type;
+        key.insert(key.end(), {b->channel, b->F, b->frame_type, est ? 1 : 0});
+    }
+    for (int i = 0; i < n; ++i) io[i].lay = &lays[i];
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventSynchronize(js[i].ev_start);   // frames reusable
+    int rc = e == cudaSuccess ? SM_OK : cuda_fail(e, "staging batch");
+    if (rc == SM_OK) {
+        std::lock_guard<std::mutex> lk(h->launch_mu);
+        cudaStream_t st = h->streams[js[0].slot];
+        if (h->ordered) e = cudaStreamWaitEvent(st, h->order, 0);
+        for (int i = 1; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(st, js[i].ev_start, 0);
+        for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventRecord(js[i].ev_start, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ordering batch");
+        sm_batch* bt = nullptr;
+        if (rc == SM_OK) {
+            std::vector<int> ckey(key.begin(), key.end());
+            for (int i = 0; i < n; ++i) ckey[4 * i + 3] = 0;       // the STF mode does not change the queue
+            auto it = h->batches.find(ckey);
+            if (it != h->batches.end()) {
+                bt = it->second;
+            } else {
+                rc = sm_batch_create(n, plans.data(), Fs.data(), fts.data(), nullptr, &bt);
+                if (rc == SM_OK) h->batches[ckey] = bt;
+            }
+        }
+        // one graph per batch composition and placement (every pointer its
+        // kernels take is fixed by the bursts' arena offsets)
+        if (rc == SM_OK) {
+            std::vector<size_t> gk(key.begin(), key.end());
+            for (int i = 0; i < n; ++i) gk.push_back(js[i].off);
+            gk.push_back((size_t)js[0].slot);
+            sm_handle::Graph* gr = nullptr;
+            {
+                std::lock_guard<std::mutex> lk2(h->mu);
+                auto it = h->bgraphs.find(gk);
+                if (it != h->bgraphs.end()) gr = &it->second;
+            }
+            if (!gr) {
+                sm_handle::Graph ng;
+                e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "cudaStreamBeginCapture");
+                } else {
+                    rc = sm_batch_reconstruct(bt, io.data(), st);
+                    cudaGraph_t graph = nullptr;
+                    e = cudaStreamEndCapture(st, &graph);
+                    if (rc == SM_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture");
+                    if (rc == SM_OK) {
+                        e = cudaGraphInstantiate(&ng.exec, graph, 0);
+                        if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+                    }
+                    if (graph) cudaGraphDestroy(graph);
+                }
+                if (rc == SM_OK) {
+                    std::lock_guard<std::mutex> lk2(h->mu);
+                    gr = &(h->bgraphs[gk] = std::move(ng));
+                }
+            }
+            if (rc == SM_OK) rc = ret(cudaGraphLaunch(gr->exec, st), "cudaGraphLaunch");
+        }
+        if (rc == SM_OK) {
+            e = cudaEventRecord(h->order, st);
+            h->ordered = e == cudaSuccess;
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
+        }
+        for (int i = 0; i < n && rc == SM_OK; ++i) {
+            js[i].batch = bt;
+            rc = copy_back(h, js[i], h->ch[bs[i].channel], st);
+            if (rc == SM_OK) rc = ret(cudaEventRecord(js[i].ev_done, st), "cudaEventRecord");
+        }
+    }
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (rc != SM_OK) {
+        for (auto& j : js) {
+            if (j.slot >= 0) cudaStreamSynchronize(h->streams[j.slot]);
+            finish_job(h, j);
+        }
+        return rc;
+    }
+    const double now = ms_since(h->t0);
+    for (int i = 0; i < n; ++i) {
+        js[i].t_submit = now;
+        tickets[i] = js[i].ticket;
+        h->jobs[js[i].ticket] = js[i];
+    }
+    return SM_OK;
+}
+
 extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result* res) {
     if (!h) { set_error("NULL handle"); return SM_EINVAL; }
     const auto start = Clock::now();
@@ -1138,6 +1334,7 @@ extern "C" int sm_poll(sm_handle* h, uint64_t ticket, int timeout_ms, sm_result*
         }
     }
     int rc = SM_OK;
+    if (j.batch && sm_batch_status(j.batch) != SM_OK) rc = SM_ECUDA;
     if (res) {
         res->status = rc;
         res->t_submit_ms = j.t_submit;
@@ -1161,6 +1358,10 @@ extern "C" int sm_close(sm_handle* h) {
         for (auto& kv : h->jobs) finish_job(h, kv.second);
         h->jobs.clear();
     }
+    for (auto& kv : h->bgraphs) cudaGraphExecDestroy(kv.second.exec);
+    h->bgraphs.clear();
+    for (auto& kv : h->batches) sm_batch_destroy(kv.second);
+    h->batches.clear();
     for (auto& kv : h->graphs) {
         cudaGraphExecDestroy(kv.second.exec);
         for (auto ev : kv.second.marks) cudaEventDestroy(ev);

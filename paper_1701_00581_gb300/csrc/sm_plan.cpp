@@ -68,7 +68,7 @@ int validate_channel(const sm_channel* ch) {
     if (ch->phase_weight != SM_W_BISPEC && ch->phase_weight != SM_W_UNIT && ch->phase_weight != SM_W_SNR) {
         set_error("phase_weight must be SM_W_BISPEC, SM_W_UNIT or SM_W_SNR"); return SM_EINVAL;
     }
-    if (ch->max_frames < 1) { set_error("max_frames must be >= 1"); return SM_EINVAL; }
+    if (ch->max_frames < 1 || ch->max_frames > 65535) { set_error("max_frames must be in 1..65535"); return SM_EINVAL; }
     if (ch->acc_mode != SM_ACC_PLAIN && ch->acc_mode != SM_ACC_KAHAN) {
         set_error("acc_mode must be SM_ACC_PLAIN or SM_ACC_KAHAN"); return SM_EINVAL;
     }

@@ -207,3 +207,29 @@ def test_grid_launch_equals_the_stage_kernels(torch, bursts, mixed):
         v = plan.views(io["ws"], io["lay"], spec.F, n)
         assert np.array_equal(v["spec"].cpu().numpy(), mixed[nm]["spec"])
         assert np.array_equal(v["B"].cpu().numpy(), mixed[nm]["B"])
+
+
+def test_batch_is_captured_in_a_cuda_graph(torch, bursts, mixed):
+    """The whole batched reconstruction -- the queue reset, the batched
+    launch, the status copy and every burst's remaining stages -- is captured
+    once in a CUDA graph on a side stream and replayed twice: each replay
+    gives bitwise the eager result."""
+    from paper_1701_00581_gb300 import Batch, SM_F32, SM_U16
+    setups = [_setup(torch, nm, bursts[nm]) for nm in ORDER]
+    fts = [SM_U16 if CASES[nm][0].counts else SM_F32 for nm in ORDER]
+    bt = Batch([p for p, _ in setups], [CASES[nm][0].F for nm in ORDER], fts, **mixed["opts"])
+    ios = [io for _, io in setups]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        bt.reconstruct(ios, side)
+    for _ in range(2):
+        for io in ios:
+            io["out"].zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert bt.status() == 0
+        for nm, io in zip(ORDER, ios):
+            assert np.array_equal(io["out"].cpu().numpy(), mixed[nm]["out"])
+    bt.close()

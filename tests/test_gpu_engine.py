@@ -375,5 +375,45 @@ def test_pipelined_mode_needs_two_workspaces(torch):
         Engine([ch], hbm_budget_bytes=4 << 30, max_inflight=2, overlap_kernels=2)
     assert e.value.status == _lib.SM_ENOMEM
     with pytest.raises(SpeckleError) as e:
-        Engine([ch], hbm_budget_bytes=4 << 30, max_inflight=2, overlap_kernels=3)
+        Engine([ch], hbm_budget_bytes=4 << 30, max_inflight=2, overlap_kernels=4)
     assert e.value.status == _lib.SM_EINVAL
+
+
+def test_batched_engine_mode(torch):
+    """overlap_kernels = 3: bursts of two channels submitted as one batch run
+    through one batched launch; each burst equals itself submitted alone in
+    that mode (bitwise), and the plain stage path to rounding (the batched
+    launch may place the transforms differently); a single submit is a
+    batch of one; a batch larger than the free slots is refused whole."""
+    from paper_1701_00581_gb300 import Channel, Engine, SpeckleError, _lib
+    c0 = CS.gpu_channel("ragged")
+    c1 = Channel(W=96, H=80, N=64, R=6, stride=32, taper=8, max_frames=5)
+    bursts = _bursts(2)
+    b1 = S.make_burst(S.BurstSpec(W=96, H=80, F=5, N=64, dr0=(4.0, 6.0), counts=True), channel=12)
+    eng = Engine([c0, c1], hbm_budget_bytes=2 << 30, max_inflight=4, overlap_kernels=3)
+    items = [dict(channel=0, frames=bursts[0]["frames"], out=np.zeros((110, 150), np.float32),
+                  valid=np.zeros((110, 150), np.uint8), d_over_r0=bursts[0]["d_over_r0"]),
+             dict(channel=1, frames=b1["frames"], out=np.zeros((80, 96), np.float32), d_over_r0=b1["d_over_r0"]),
+             dict(channel=0, frames=bursts[1]["frames"], out=np.zeros((110, 150), np.float32))]   # seeing estimated
+    tickets = eng.submit_batch(items)
+    assert len(set(tickets)) == 3
+    for t in tickets:
+        st, res = eng.poll(t, -1)
+        assert st == 0 and res["gpu_ms"] > 0
+    alone = []
+    for it in items:
+        o = np.zeros_like(it["out"])
+        t = eng.submit_batch([dict(it, out=o, valid=None)])[0]
+        assert eng.poll(t, -1)[0] == 0
+        alone.append(o)
+    with pytest.raises(SpeckleError) as e:
+        eng.submit_batch([dict(items[0], out=np.zeros((110, 150), np.float32))] * 5)
+    assert e.value.status == _lib.SM_EBUSY
+    eng.close()
+    for it, a in zip(items, alone):
+        assert np.array_equal(it["out"], a)
+    ref0, v0 = _plain(torch, c0, bursts[0])
+    assert np.array_equal(items[0]["valid"].astype(bool), v0)
+    assert CS.rel_l2(items[0]["out"][v0], ref0[v0]) < 1e-5
+    ref1, v1 = _plain(torch, c1, b1)
+    assert CS.rel_l2(items[1]["out"][v1], ref1[v1]) < 1e-5
