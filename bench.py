@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--spectra", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="frame-spectra storage (precision sweep)")
     ap.add_argument("--acc", default="plain", choices=["plain", "kahan"], help="bispectrum sums")
-    ap.add_argument("--phase", default="fp32", choices=["fp32", "fp64"], help="recursion arithmetic")
+    ap.add_argument("--phase", default="fp32", choices=["fp32", "fp64", "ff"], help="recursion arithmetic (ff: float-float)")
     ap.add_argument("--weight", default="bispec", choices=["bispec", "unit", "snr"], help="phase-term weighting")
     ap.add_argument("--iters", type=int, default=0, help="least-squares phase sweeps after the recursion")
     ap.add_argument("--inflight", type=int, default=2, help="bursts in flight on the served e2e path")
@@ -252,16 +252,20 @@ def kernel_sha256() -> str:
     return h.hexdigest()
 
 
-def kernel_traffic(units_per_launch: float):
+def kernel_traffic(units_per_launch: float, shape: dict):
     """DRAM bytes (read + write) per launch of the dominant kernel from the
     committed ncu summary, scaled from the captured case to this launch by
     the units processed; None when the kernel source changed since the
-    counters were taken (the summary records the sources' SHA-256)."""
+    counters were taken (the summary records the sources' SHA-256) or when
+    this launch's subfield shape (N, R, F, spectra storage, sums) is not the
+    captured one, since the bytes per subfield depend on all five."""
     path = os.path.join(ROOT, "profiles", "k_bispectrum_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     if rec.get("source_sha256") != kernel_sha256():
+        return None
+    if any(rec.get("shape", {}).get(k) != v for k, v in shape.items()):
         return None
     return rec["dram_bytes_per_unit"] * units_per_launch
 
@@ -470,11 +474,11 @@ def main():
     b = make_burst(spec, channel=1, burst=rank, device=f"cuda:{local}")
     F = spec.F
     from paper_1701_00581_gb300 import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_FP16, SM_FP32,
-                                        SM_PHASE_FP32, SM_PHASE_FP64, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT,
+                                        SM_PHASE_FF, SM_PHASE_FP32, SM_PHASE_FP64, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT,
                                         SM_EDGE_DROP, SM_MOSAIC_CENTRAL)
     modes = dict(spectra_prec={"fp32": SM_FP32, "fp16": SM_FP16, "bf16": SM_BF16}[args.spectra],
                  acc_mode={"plain": SM_ACC_PLAIN, "kahan": SM_ACC_KAHAN}[args.acc],
-                 phase_prec={"fp32": SM_PHASE_FP32, "fp64": SM_PHASE_FP64}[args.phase],
+                 phase_prec={"fp32": SM_PHASE_FP32, "fp64": SM_PHASE_FP64, "ff": SM_PHASE_FF}[args.phase],
                  phase_weight={"bispec": SM_W_BISPEC, "unit": SM_W_UNIT, "snr": SM_W_SNR}[args.weight],
                  phase_iters=args.iters)
     if args.layout == "paper":
@@ -542,7 +546,7 @@ def main():
     if os.path.exists(peaks_path):
         sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max))
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    traffic = kernel_traffic(n_sub)
+    traffic = kernel_traffic(n_sub, {"N": info["N"], "R": info["R"], "F": F, "spectra": args.spectra, "acc": args.acc})
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": None if traffic is None else int(traffic),

@@ -77,6 +77,8 @@ extern "C" {
 
 #define SM_PHASE_FP32 0   /* phase recursion arithmetic FP32, phasors stored FP64 */
 #define SM_PHASE_FP64 1   /* phase recursion arithmetic FP64 throughout       */
+#define SM_PHASE_FF   2   /* phase recursion arithmetic float-float (about 48
+                           * significant bits) on the FP32 pipe               */
 
 /* ---- one camera channel ------------------------------------------------ */
 typedef struct {
@@ -91,7 +93,7 @@ typedef struct {
     double ck;            /* Korff constant of the model STF (e.g. 0.435)      */
     int    max_frames;    /* largest burst length F accepted (>= 1)            */
     int    acc_mode;      /* SM_ACC_PLAIN / SM_ACC_KAHAN                       */
-    int    phase_prec;    /* SM_PHASE_FP32 / SM_PHASE_FP64                     */
+    int    phase_prec;    /* SM_PHASE_FP32 / SM_PHASE_FP64 / SM_PHASE_FF       */
     int    phase_iters;   /* least-squares sweeps after the recursion (0..64);
                            * see sm_stage_phase                               */
     int    edge_mode;     /* SM_EDGE_PAD / SM_EDGE_DROP                        */

@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BATCH_FUSED, SM_BATCH_GRID, SM_BATCH_TILES, SM_BF16, SM_EDGE_DROP, SM_EDGE_PAD, SM_F32,  # noqa: F401
                    SM_FP16, SM_FP32, SM_MOSAIC_BLEND, SM_MOSAIC_CENTRAL,
-                   SM_PHASE_FP32, SM_PHASE_FP64, SM_U16, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT, SpeckleError,
+                   SM_PHASE_FF, SM_PHASE_FP32, SM_PHASE_FP64, SM_U16, SM_W_BISPEC, SM_W_SNR, SM_W_UNIT, SpeckleError,
                    check, load)
 
 __all__ = ["Channel", "Plan", "Batch", "Engine", "load", "SpeckleError"]

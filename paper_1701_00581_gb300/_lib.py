@@ -19,7 +19,7 @@ SM_FP32, SM_FP16, SM_BF16 = 0, 1, 2
 SM_W_BISPEC, SM_W_UNIT, SM_W_SNR = 0, 1, 2
 SM_U16, SM_F32 = 0, 1
 SM_ACC_PLAIN, SM_ACC_KAHAN = 0, 1
-SM_PHASE_FP32, SM_PHASE_FP64 = 0, 1
+SM_PHASE_FP32, SM_PHASE_FP64, SM_PHASE_FF = 0, 1, 2
 SM_EDGE_PAD, SM_EDGE_DROP = 0, 1
 SM_MOSAIC_BLEND, SM_MOSAIC_CENTRAL = 0, 1
 SM_BATCH_FUSED, SM_BATCH_TILES, SM_BATCH_GRID = 1, 2, 3

@@ -42,6 +42,76 @@ template <> struct Cx<double> {
     __device__ static double rnorm(double n2) { return 1.0 / sqrt(n2); }
 };
 
+// Float-float ("double-single") numbers: an unevaluated sum hi + lo of two
+// floats, |lo| <= ulp(hi) / 2, with about 48 significant bits, computed on
+// the FP32 pipe -- GB300's FP64 unit runs at a small fraction of its FP32
+// rate.  The error-free transformations are Knuth's two-sum, Dekker's
+// fast-two-sum and the FMA-based two-product (the product's exact low part
+// is fma(a, b, -a b)); addition and multiplication are the classical
+// double-single ones, division and the reciprocal square root one Newton
+// correction of the float estimate.  The type and its functions live in a
+// namespace of their own: argument-dependent lookup adds them to the
+// overloads of sqrt and __shfl_xor_sync without hiding the built-in ones.
+namespace ffa {
+struct ff {
+    float hi, lo;
+    __device__ ff() : hi(0.f), lo(0.f) {}
+    __device__ ff(int v) : hi((float)v), lo(0.f) {}
+    __device__ ff(float v) : hi(v), lo(0.f) {}
+    __device__ ff(float h, float l) : hi(h), lo(l) {}
+    __device__ explicit ff(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {       // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return ff(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    return ff(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v)));
+}
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    return fast_two_sum(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ ff operator/(ff a, ff b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const ff r = a - b * ff(q1);
+    return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
+__device__ __forceinline__ ff& operator/=(ff& a, ff b) { return a = a / b; }
+__device__ __forceinline__ bool operator>(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ ff sqrt(ff a) {
+    if (!(a.hi > 0.f)) return ff(0.f);
+    const float s = sqrtf(a.hi);
+    const ff r = a - ff(s) * ff(s);                  // exact residual of s^2
+    return fast_two_sum(s, __fdiv_rn(r.hi, 2.f * s));
+}
+__device__ __forceinline__ ff __shfl_xor_sync(unsigned mask, ff v, int o) {
+    return ff(::__shfl_xor_sync(mask, v.hi, o), ::__shfl_xor_sync(mask, v.lo, o));
+}
+}  // namespace ffa
+using ffa::ff;
+struct ff2 { ff x, y; };
+template <> struct Cx<ff> {
+    using T2 = ff2;
+    __device__ static ff2 make(ff x, ff y) { return ff2{x, y}; }
+    // 1 / sqrt(n2): the float estimate r, then r (3 - n2 r^2) / 2 in float-float
+    __device__ static ff rnorm(ff n2) {
+        const ff r(rsqrtf(n2.hi));
+        return r * (ff(3.f) - n2 * r * r) * ff(0.5f);
+    }
+};
+
 // z of any frequency from the half-box copy (row 0 holds both signs).
 template <typename T2>
 __device__ __forceinline__ T2 zget(const T2* zs, int pitch, int K, int kx, int ky) {
@@ -298,7 +368,7 @@ namespace smk {
 size_t phase_smem_bytes(int hb_rows, int box_pitch, int max_ring_items, int max_ring_points, int phase_prec) {
     size_t a, b, c;
     return phase_layout(hb_rows, box_pitch, max_ring_items, max_ring_points,
-                        phase_prec == SM_PHASE_FP64 ? sizeof(double2) : sizeof(float2), &a, &b, &c);
+                        phase_prec == SM_PHASE_FP32 ? sizeof(float2) : 16, &a, &b, &c);
 }
 
 cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const float2* M, const float* P,
@@ -309,6 +379,10 @@ cudaError_t launch_phase(const smi::PlanDev& p, int nsub, const float2* B, const
         e = cudaFuncSetAttribute(k_phase<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         k_phase<double, 512><<<nsub, 512, sm, st>>>(p, B, M, P, z);
+    } else if (p.phase_prec == SM_PHASE_FF) {
+        e = cudaFuncSetAttribute(k_phase<ff, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_phase<ff, 512><<<nsub, 512, sm, st>>>(p, B, M, P, z);
     } else if (threads == 256) {
         e = cudaFuncSetAttribute(k_phase<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;

@@ -86,8 +86,8 @@ int validate_channel(const sm_channel* ch) {
     if (ch->mosaic_mode == SM_MOSAIC_CENTRAL && (ch->edge_mode != SM_EDGE_DROP || (ch->N - ch->stride) % 2)) {
         set_error("SM_MOSAIC_CENTRAL needs SM_EDGE_DROP and N - stride even"); return SM_EINVAL;
     }
-    if (ch->phase_prec != SM_PHASE_FP32 && ch->phase_prec != SM_PHASE_FP64) {
-        set_error("phase_prec must be SM_PHASE_FP32 or SM_PHASE_FP64"); return SM_EINVAL;
+    if (ch->phase_prec != SM_PHASE_FP32 && ch->phase_prec != SM_PHASE_FP64 && ch->phase_prec != SM_PHASE_FF) {
+        set_error("phase_prec must be SM_PHASE_FP32, SM_PHASE_FP64 or SM_PHASE_FF"); return SM_EINVAL;
     }
     if (!(ch->ck >= 0.0)) { set_error("ck must be >= 0"); return SM_EINVAL; }
     if (smk::spectra_smem_bytes(ch->N, K) > 227 * 1024) {

@@ -79,7 +79,7 @@ def test_strerror(lib):
 @pytest.mark.parametrize("field,value", [
     ("N", 100), ("N", 512), ("R", 0), ("R", 40), ("fc", 0.0), ("fc", 0.5), ("taper", 40),
     ("stride", 0), ("spectra_prec", 3), ("phase_weight", 3), ("max_frames", 0), ("W", 0),
-    ("acc_mode", 2), ("phase_prec", 2), ("phase_iters", -1), ("phase_iters", 65)])
+    ("acc_mode", 2), ("phase_prec", 3), ("phase_iters", -1), ("phase_iters", 65)])
 def test_plan_create_rejects_bad_channels(lib, field, value):
     from paper_1701_00581_gb300 import Channel
     ch = Channel(W=256, H=256, N=128, R=16).to_c()

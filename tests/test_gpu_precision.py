@@ -1,13 +1,14 @@
 """Precision modes on the GPU: the precision sweep.
 
 Frame spectra stored in FP32, FP16 (with a 2^14 scale) or BF16; bispectrum
-sums in plain or compensated (Kahan) FP32; recursion arithmetic in FP32 or
-FP64.  The per-stage error against the FP64 oracle is measured and gated:
+sums in plain or compensated (Kahan) FP32; recursion arithmetic in FP32,
+FP64 or float-float (pairs of FP32 numbers, about 48 significant bits).  The per-stage error against the FP64 oracle is measured and gated:
 Every storage mode is held to the 1e-3 image tolerance of the mixed-precision
 path; the per-stage spectra gates follow the mantissa (FP16 keeps 11
 significant bits, BF16 8) and are reported.  Two tests
 isolate the modes: Kahan sums against the exact sum of the same FP32
-spectra, and the FP64 recursion against the oracle's on the same B and M.
+spectra, and the FP64 and float-float recursions against the oracle's on the
+same B and M.
 """
 import os
 
@@ -15,8 +16,8 @@ import numpy as np
 import pytest
 
 from oracle import speckle_oracle as O
-from paper_1701_00581_gb300 import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_FP16, SM_FP32, SM_PHASE_FP32,
-                                    SM_PHASE_FP64)
+from paper_1701_00581_gb300 import (SM_ACC_KAHAN, SM_ACC_PLAIN, SM_BF16, SM_FP16, SM_FP32, SM_PHASE_FF,
+                                    SM_PHASE_FP32, SM_PHASE_FP64)
 
 from . import _cases as CS
 
@@ -73,6 +74,8 @@ MODES = [  # (spectra storage, bispectrum sums, recursion arithmetic)
     (SM_FP32, SM_ACC_KAHAN, SM_PHASE_FP64),
     (SM_FP16, SM_ACC_KAHAN, SM_PHASE_FP64),
     (SM_BF16, SM_ACC_KAHAN, SM_PHASE_FP64),
+    (SM_FP32, SM_ACC_PLAIN, SM_PHASE_FF),
+    (SM_FP16, SM_ACC_KAHAN, SM_PHASE_FF),
 ]
 
 
@@ -146,12 +149,12 @@ def _oracle_B_from_gpu(plan, Bg, N, R):
 
 def test_fp64_recursion_matches_the_oracle_on_the_same_inputs(torch):
     """Recursion alone: the oracle's FP64 recursion on the GPU's own B and M
-    against the GPU recursion in FP64 and in FP32 arithmetic."""
+    against the GPU recursion in FP64, float-float and FP32 arithmetic."""
     from paper_1701_00581_gb300 import Plan
     b = CS.burst("ragged")
     N, R = 64, 8
     err = {}
-    for phase in (SM_PHASE_FP32, SM_PHASE_FP64):
+    for phase in (SM_PHASE_FP32, SM_PHASE_FP64, SM_PHASE_FF):
         plan = Plan(CS.gpu_channel("ragged", phase_prec=phase))
         g = CS.gpu_run(plan, b["frames"], b["stf_emp"])
         K = plan.info["K"]
@@ -170,6 +173,7 @@ def test_fp64_recursion_matches_the_oracle_on_the_same_inputs(torch):
     if report:
         with open(os.path.join(report, "precision_recursion.txt"), "w") as f:
             f.write(f"max |z_gpu - z_fp64 oracle| on the same B, M: FP32 arithmetic {err[SM_PHASE_FP32]:.3e}, "
-                    f"FP64 arithmetic {err[SM_PHASE_FP64]:.3e}\n")
+                    f"FP64 arithmetic {err[SM_PHASE_FP64]:.3e}, float-float {err[SM_PHASE_FF]:.3e}\n")
     assert err[SM_PHASE_FP64] < 1e-9
+    assert err[SM_PHASE_FF] < 1e-9
     assert err[SM_PHASE_FP32] < 1e-3

@@ -3,7 +3,7 @@ subfields of 256^2, |v| <= 24).
 
 Every precision mode of the path -- frame spectra stored in FP32, FP16
 (scaled by 2^14) or BF16; bispectrum sums plain or compensated (Kahan);
-recursion arithmetic FP32 or FP64 -- runs the whole burst on the GPU with
+recursion arithmetic FP32, FP64 or float-float -- runs the whole burst on the GPU with
 the same model STF, and is compared with the FP64 oracle on a fixed sample
 of 16 subfields (two 2 x 2 blocks, the 2 x 2 block at the origin, four
 ragged 256 x 240 subfields of the bottom row).  Per stage:
@@ -119,23 +119,25 @@ def _errors(tio, g):
 
 
 def _mode_name(m):
-    from paper_1701_00581_gb300 import SM_ACC_KAHAN, SM_BF16, SM_FP16, SM_PHASE_FP64
+    from paper_1701_00581_gb300 import SM_ACC_KAHAN, SM_BF16, SM_FP16, SM_PHASE_FF, SM_PHASE_FP64
     return (f"spectra {dict([(0, 'FP32'), (SM_FP16, 'FP16'), (SM_BF16, 'BF16')])[m.get('spectra_prec', 0)]}, "
             f"sums {'Kahan' if m.get('acc_mode') == SM_ACC_KAHAN else 'plain'}, "
-            f"recursion {'FP64' if m.get('phase_prec') == SM_PHASE_FP64 else 'FP32'}")
+            f"recursion {dict([(0, 'FP32'), (SM_PHASE_FP64, 'FP64'), (SM_PHASE_FF, 'float-float')])[m.get('phase_prec', 0)]}")
 
 
 def _modes():
-    from paper_1701_00581_gb300 import SM_ACC_KAHAN, SM_BF16, SM_FP16, SM_PHASE_FP64
+    from paper_1701_00581_gb300 import SM_ACC_KAHAN, SM_BF16, SM_FP16, SM_PHASE_FF, SM_PHASE_FP64
     # (modes, (P gate, bispectrum phase gate in rad, sub-image gate))
     return [({}, (1e-4, 1e-4, 1e-3)), (dict(spectra_prec=SM_FP16), (1e-3, 1e-3, 1e-3)),
             (dict(spectra_prec=SM_BF16), (1e-2, 1e-2, 2e-3)),
             (dict(acc_mode=SM_ACC_KAHAN), (1e-4, 1e-4, 1e-3)), (dict(phase_prec=SM_PHASE_FP64), (1e-4, 1e-4, 1e-3)),
             (dict(spectra_prec=SM_FP16, acc_mode=SM_ACC_KAHAN, phase_prec=SM_PHASE_FP64), (1e-3, 1e-3, 1e-3)),
-            (dict(spectra_prec=SM_BF16, acc_mode=SM_ACC_KAHAN, phase_prec=SM_PHASE_FP64), (1e-2, 1e-2, 2e-3))]
+            (dict(spectra_prec=SM_BF16, acc_mode=SM_ACC_KAHAN, phase_prec=SM_PHASE_FP64), (1e-2, 1e-2, 2e-3)),
+            (dict(phase_prec=SM_PHASE_FF), (1e-4, 1e-4, 1e-3)),
+            (dict(spectra_prec=SM_FP16, phase_prec=SM_PHASE_FF), (1e-3, 1e-3, 1e-3))]
 
 
-@pytest.mark.parametrize("k", range(7))
+@pytest.mark.parametrize("k", range(9))
 def test_precision_mode_on_the_tio_burst(torch, tio, k):
     modes, (gP, gB, gI) = _modes()[k]
     eP, eB, eI, eM = _errors(tio, _gpu(torch, tio, **modes))
