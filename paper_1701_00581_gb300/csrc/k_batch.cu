@@ -271,7 +271,7 @@ k_batch(const __grid_constant__ BatchArgs a, const int4* __restrict__ items, int
 // only the bursts' buffers are looked up by blockIdx.z.
 template <int PREC, bool VCH>
 __global__ void __launch_bounds__(BT, 4) k_batch_grid(PlanDev p, const __grid_constant__ smi::BatchPtrs q) {
-    __shared__ __align__(16) float2 S[2 * smb::staging_frames<PREC>() * smb::BUF];
+    __shared__ __align__(16) float2 S[smb::staging_float2<PREC>()];
     const int z = blockIdx.z;
     smb::bispec_tile<PREC, VCH, false>(p, q.spec[z], q.F[z], q.B[z], blockIdx.x, blockIdx.y, S);
 }
@@ -289,7 +289,7 @@ size_t fft_smem_for(int N, int K) {
 namespace smk {
 
 size_t batch_smem_bytes(int N, int K, int prec) {
-    const size_t bis = (size_t)2 * (prec == SM_FP32 ? 4 : 1) * smb::BUF * sizeof(float2);
+    const size_t bis = smb::staging_bytes(prec);
     const size_t fft = N > 0 ? fft_smem_for(N, K) : 0;
     return bis > fft ? bis : fft;
 }

@@ -38,7 +38,7 @@ using smb::THREADS;
 template <int PREC, bool VCH, bool KAHAN>
 __global__ void __launch_bounds__(THREADS, 4)
 k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict__ B) {
-    __shared__ __align__(16) float2 S[2 * smb::staging_frames<PREC>() * BUF];
+    __shared__ __align__(16) float2 S[smb::staging_float2<PREC>()];
     smb::bispec_tile<PREC, VCH, KAHAN>(p, spec, F, B, blockIdx.x, blockIdx.y, S);
 }
 

@@ -139,10 +139,11 @@ __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, 
 // outside the box), FB frames per stage in a two-stage ring, so one barrier
 // serves FB frames.  FP32 values (E = 8 bytes) are multiplied out from the
 // ring itself.  Half-precision values (E = 4: half2 or bfloat162) are
-// copied raw, at half the bytes, and converted to FP32 once per stage into a
-// compute buffer (a second barrier per stage), so the inner loop is the same
-// as for FP32.  The ring and the compute buffer of the half-precision path
-// fill the same 2 FB BUF float2 of shared memory as the FP32 ring.
+// copied raw, at half the bytes, and converted to FP32 once per stage into
+// one of two compute buffers, a stage ahead of the products, so the inner
+// loop and the barrier count are those of FP32.  Shared memory per CTA:
+// 2 FB BUF float2 (FP32 ring), or a 2 FB BUF raw ring and 2 FB BUF float2
+// of compute buffers (half precision).
 template <int PREC> struct Staging;
 template <> struct Staging<SM_FP32> { static constexpr bool ASYNC = true; static constexpr int FB = 4, E = 8; };
 template <> struct Staging<SM_FP16> { static constexpr bool ASYNC = true; static constexpr int FB = 4, E = 4; };
@@ -241,7 +242,7 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
         const Word* sp = reinterpret_cast<const Word*>(spec) + sbase;
         const int nst = (F + FB - 1) / FB;
         // The ring: E-byte slots, 2 stages x FB frames x BUF; the half-
-        // precision compute buffer (FB x BUF float2) follows it.
+        // precision compute buffers (2 x FB x BUF float2) follow it.
         Word* ring = reinterpret_cast<Word*>(S);
         float2* cbuf = S + FB * BUF;
         // Copy slots, fixed for the CTA: global source at frame 0, shared
@@ -304,19 +305,35 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
                 for (int k = 0; k < (KAHAN ? NC : 1); ++k) comp[j][k] = make_float2(0.f, 0.f);
             }
             if (pass > 0) __syncthreads();             // the previous pass is done with the ring
+            // Half precision converts stage st + 1 while stage st is
+            // multiplied out, so one barrier per stage serves both: at the
+            // barrier of iteration st the raw stage st + 1 has landed, the
+            // conversion of stage st (into compute buffer st & 1) is complete
+            // and the products of stage st - 1 are done with compute buffer
+            // (st + 1) & 1.  The raw ring slot st & 1 is refilled with stage
+            // st + 2, its conversion having finished before the barrier.
+            auto convert = [&](int st) {
+                const unsigned* rs = reinterpret_cast<const unsigned*>(ring) + (st & 1) * FB * BUF;
+                float2* cb = cbuf + (st & 1) * FB * BUF;
+                for (int e = tid; e < FB * BUF; e += THREADS) cb[e] = raw_to_float2<PREC>(rs[e]);
+            };
             issue(0);
+            if constexpr (RAW) {
+                issue(1);
+                asm volatile("cp.async.wait_group 1;");
+                __syncthreads();                      // raw stage 0 visible
+                convert(0);
+            }
             for (int st = 0; st < nst; ++st) {
                 asm volatile("cp.async.wait_group 0;");
                 __syncthreads();          // stage st visible to all; stage st-1 fully consumed
-                issue(st + 1);
                 const float2* Sst;
                 if constexpr (RAW) {
-                    // the stage's values to FP32, once, for every warp
-                    const unsigned* rs = reinterpret_cast<const unsigned*>(ring) + (st & 1) * FB * BUF;
-                    for (int e = tid; e < FB * BUF; e += THREADS) cbuf[e] = raw_to_float2<PREC>(rs[e]);
-                    __syncthreads();
-                    Sst = cbuf;
+                    issue(st + 2);
+                    if (st + 1 < nst) convert(st + 1);
+                    Sst = cbuf + (st & 1) * FB * BUF;
                 } else {
+                    issue(st + 1);
                     Sst = reinterpret_cast<const float2*>(ring) + (st & 1) * FB * BUF;
                 }
                 if (!pm) continue;
@@ -338,5 +355,12 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
 
 
 template <int PREC> __host__ __device__ constexpr int staging_frames() { return Staging<PREC>::FB; }
+// float2 elements of the staging area bispec_tile<PREC> takes
+template <int PREC> __host__ __device__ constexpr int staging_float2() {
+    return Staging<PREC>::E == 8 ? 2 * Staging<PREC>::FB * BUF : 3 * Staging<PREC>::FB * BUF;
+}
+__host__ __device__ constexpr size_t staging_bytes(int prec) {
+    return (size_t)(prec == SM_FP32 ? staging_float2<SM_FP32>() : staging_float2<SM_FP16>()) * 8;
+}
 
 }  // namespace smb

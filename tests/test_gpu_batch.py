@@ -50,10 +50,10 @@ def bursts():
     return out
 
 
-def _setup(torch, name, b):
+def _setup(torch, name, b, **modes):
     from paper_1701_00581_gb300 import Channel, Plan
     spec, N, R, given = CASES[name]
-    plan = Plan(Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=spec.F))
+    plan = Plan(Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=spec.F, **modes))
     dev = "cuda:0"
     n = plan.info["n_sub"]
     ws, lay = plan.workspace(spec.F, n)
@@ -233,3 +233,40 @@ def test_batch_is_captured_in_a_cuda_graph(torch, bursts, mixed):
         for nm, io in zip(ORDER, ios):
             assert np.array_equal(io["out"].cpu().numpy(), mixed[nm]["out"])
     bt.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_half_precision_batches_match_the_stage_kernels(torch, bursts, prec):
+    """Spectra stored in FP16 or BF16: the batched launches stage the raw
+    half-precision values, convert them a stage ahead and run the FP32 tile
+    body, in every launch shape.  With the transforms placed first the
+    bispectrum is bitwise that of the per-stage kernels; the fused launch's
+    own transforms round the FP32 spectra differently before storage, which
+    moves B by at most a half-precision rounding step."""
+    from paper_1701_00581_gb300 import SM_BATCH_FUSED, SM_BATCH_GRID, SM_BATCH_TILES, SM_BF16, SM_F32, SM_FP16, \
+        SM_U16, Batch
+    mode = {"fp16": SM_FP16, "bf16": SM_BF16}[prec]
+    tol = {"fp16": 2e-3, "bf16": 2e-2}[prec]
+    fts = [SM_U16 if CASES[nm][0].counts else SM_F32 for nm in ORDER]
+    ref = {}
+    for nm in ORDER:
+        spec = CASES[nm][0]
+        plan, io = _setup(torch, nm, bursts[nm], spectra_prec=mode)
+        n = plan.info["n_sub"]
+        plan.stage_spectra(io["frames"], spec.F, 0, n, io["ws"], io["lay"])
+        plan.stage_bispectrum(spec.F, n, io["ws"], io["lay"])
+        torch.cuda.synchronize()
+        ref[nm] = plan.views(io["ws"], io["lay"], spec.F, n)["B"].cpu().numpy()
+    for launch in (SM_BATCH_FUSED, SM_BATCH_TILES, SM_BATCH_GRID):
+        setups = [_setup(torch, nm, bursts[nm], spectra_prec=mode) for nm in ORDER]
+        bt = Batch([p for p, _ in setups], [CASES[nm][0].F for nm in ORDER], fts, launch=launch)
+        bt.spectra_bispectrum([io for _, io in setups])
+        torch.cuda.synchronize()
+        assert bt.status() == 0
+        for nm, (plan, io) in zip(ORDER, setups):
+            B = plan.views(io["ws"], io["lay"], CASES[nm][0].F, plan.info["n_sub"])["B"].cpu().numpy()
+            if launch == SM_BATCH_FUSED:
+                assert CS.rel_l2(B, ref[nm]) < tol, nm
+            else:
+                assert np.array_equal(B, ref[nm]), nm
+        bt.close()

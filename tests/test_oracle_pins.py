@@ -5,6 +5,7 @@ invariant, a library routine or a hand-worked case, so that a dropped term, a
 wrong sign or index, or a transposed operand fails here.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -480,14 +481,27 @@ def test_mosaic_undoes_the_window():
 # seeing (Sect. 3.1: spectral ratio technique, von der Luehe 1984)
 # ---------------------------------------------------------------------------
 
+def _paper_values():
+    """The paper's printed numbers (tests/golden/paper_printed_values.txt)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_printed_values.txt")
+    vals = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            key, value = line.split()[:2]
+            vals[key] = int(value)
+    return vals
+
+
 def test_seeing_cubes_match_the_paper_count():
     # Sect. 3.1: a 2560 x 2160 burst gives 80 non-overlapping 256^2 cubes
-    for stride in (64, 128, 256):
-        cubes = O.seeing_cubes(2560, 2160, 256, stride)
-        assert len(cubes) == 80
-        subs = O.subfield_grid(2560, 2160, 256, stride)
+    pv = _paper_values()
+    W, H, N = pv["frame_width"], pv["frame_height"], pv["cube_size"]
+    for stride in (N // 4, N // 2, N):
+        cubes = O.seeing_cubes(W, H, N, stride)
+        assert len(cubes) == pv["seeing_cubes"]
+        subs = O.subfield_grid(W, H, N, stride)
         corners = sorted((subs[c][0], subs[c][1]) for c in cubes)
-        assert corners == sorted((x, y) for x in range(0, 2560 - 255, 256) for y in range(0, 2160 - 255, 256))
+        assert corners == sorted((x, y) for x in range(0, W - N + 1, N) for y in range(0, H - N + 1, N))
     assert len(O.seeing_cubes(1024, 1024, 128, 64)) == 64
     assert len(O.seeing_cubes(150, 110, 64, 32)) == 2          # one row of two; the rest is ragged
     assert O.seeing_cubes(60, 60, 64, 32) == []
@@ -595,15 +609,23 @@ def test_estimate_seeing_orders_bursts_by_seeing():
 # ---------------------------------------------------------------------------
 
 def test_paper_layout_matches_the_papers_counts():
-    subs = O.subfield_grid(2560, 2160, 256, 64, drop_edge=True)
-    assert len(subs) == 1110 and all(w == 256 and h == 256 for _, _, w, h in subs)
+    # Sect. 3.2 and Sect. 4: 1110 cubes of 256^2 and a 2368 x 1920 mosaic
+    pv = _paper_values()
+    W, H, N = pv["frame_width"], pv["frame_height"], pv["cube_size"]
+    subs = O.subfield_grid(W, H, N, N // 4, drop_edge=True)
+    assert len(subs) == pv["overlapping_cubes"] and all(w == N and h == N for _, _, w, h in subs)
     assert subs[-1] == (2304, 1856, 256, 256)
-    recs = [np.ones((256, 256)) for _ in subs]
-    out, valid = O.mosaic_central(recs, subs, 2560, 2160, 256, 64, 32)
+    recs = [np.ones((N, N)) for _ in subs]
+    out, valid = O.mosaic_central(recs, subs, W, H, N, N // 4, N // 8)
     ys, xs = np.nonzero(valid)
     assert (ys.min(), ys.max() + 1, xs.min(), xs.max() + 1) == (96, 2016, 96, 2464)
-    assert valid.sum() == 2368 * 1920
+    assert (xs.max() + 1 - xs.min(), ys.max() + 1 - ys.min()) == (pv["mosaic_width"], pv["mosaic_height"])
+    assert valid.sum() == pv["mosaic_width"] * pv["mosaic_height"]
     assert np.all(out[valid] == 1.0)
+    # Sect. 4: the printed bispectrum total is a whole number per cube
+    # (166 464); the paper does not give the domain behind it, so it is not
+    # matched against this path's pair count (6.46 M per cube at |v| <= 24)
+    assert pv["bispectrum_values"] % pv["overlapping_cubes"] == 0
 
 
 def test_mosaic_central_is_a_partition_by_nearest_centre():
