@@ -62,9 +62,11 @@ extern "C" {
 #define SM_F32 1          /* frame samples: float32                           */
 
 #define SM_ACC_PLAIN 0    /* bispectrum sums: FP32, one rounding per frame    */
-#define SM_ACC_KAHAN 1    /* bispectrum sums: FP32 compensated (Kahan); each
-                           * subfield streams its frames twice (half of the
-                           * offsets per pass), about 2.5x the time          */
+#define SM_ACC_KAHAN 1    /* bispectrum sums: FP32, blocked compensated: each
+                           * group of 4 frames summed plainly, the group sums
+                           * added with Kahan compensation; each subfield
+                           * streams its frames twice (half of the offsets
+                           * per pass)                                        */
 
 #define SM_EDGE_PAD  0     /* ragged last subfields kept, zero-padded to N     */
 #define SM_EDGE_DROP 1     /* full N x N subfields only (the paper's layout)   */

@@ -35,8 +35,10 @@ using smi::PlanDev;
 using smb::BUF;
 using smb::THREADS;
 
+// Four CTAs per SM (128 registers a thread); the compensated sums keep a
+// partial, a running sum and a correction per pair and take three (168).
 template <int PREC, bool VCH, bool KAHAN>
-__global__ void __launch_bounds__(THREADS, 4)
+__global__ void __launch_bounds__(THREADS, KAHAN ? 3 : 4)
 k_bispectrum(PlanDev p, const void* __restrict__ spec, int F, float2* __restrict__ B) {
     __shared__ __align__(16) float2 S[smb::staging_float2<PREC>()];
     smb::bispec_tile<PREC, VCH, KAHAN>(p, spec, F, B, blockIdx.x, blockIdx.y, S);

@@ -89,13 +89,12 @@ __device__ __forceinline__ void kahan_add(float& acc, float& c, float t) {
 }
 
 // One frame of the thread's 4 targets x NC offset columns col0 .. col0+NC-1
-// from the staged rectangles; kkmask holds those columns' bits (bit k =
-// column col0 + k).  FULL: the warp owns a used pair in every one of them,
-// so no column is tested.  KAHAN: compensated sums.
-template <bool FULL, int NC, bool KAHAN>
+// from the staged rectangles, added into acc; kkmask holds those columns'
+// bits (bit k = column col0 + k).  FULL: the warp owns a used pair in every
+// one of them, so no column is tested.
+template <bool FULL, int NC>
 __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, int wyl, int gx, int warp,
-                                                 unsigned kkmask, int col0, float2 (&acc)[4][NC],
-                                                 float2 (&comp)[4][KAHAN ? NC : 1]) {
+                                                 unsigned kkmask, int col0, float2 (&acc)[4][NC]) {
     const float4* w4 = reinterpret_cast<const float4*>(Sb + OFF_W + wyl * PW + 4 * gx);
     const float4 w01 = w4[0], w23 = w4[1];
     const float2 a[4] = {make_float2(w01.x, -w01.y), make_float2(w01.z, -w01.w),   // conj I(w)
@@ -123,13 +122,8 @@ __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, 
                 const float2 u = c[j - kk + 7];
                 const float px = fmaf(u.x, b.x, -u.y * b.y);
                 const float py = fmaf(u.x, b.y, u.y * b.x);
-                if constexpr (KAHAN) {
-                    kahan_add(acc[j][kl].x, comp[j][kl].x, fmaf(px, a[j].x, -py * a[j].y));
-                    kahan_add(acc[j][kl].y, comp[j][kl].y, fmaf(px, a[j].y, py * a[j].x));
-                } else {
-                    acc[j][kl].x = fmaf(px, a[j].x, fmaf(-py, a[j].y, acc[j][kl].x));
-                    acc[j][kl].y = fmaf(px, a[j].y, fmaf(py, a[j].x, acc[j][kl].y));
-                }
+                acc[j][kl].x = fmaf(px, a[j].x, fmaf(-py, a[j].y, acc[j][kl].x));
+                acc[j][kl].y = fmaf(px, a[j].y, fmaf(py, a[j].x, acc[j][kl].y));
             }
         }
     }
@@ -193,8 +187,11 @@ __device__ __forceinline__ void chunk_copy(const PlanDev& p, int c, int wx0, int
 // B[sl][tile]; S is the CTA's staging ring of 2 * FB * BUF float2 (16-byte
 // aligned shared memory).  Runs on 128 threads; uses __syncthreads, so the
 // whole CTA must call it.  VCH: V moves in 16-byte chunks (every tile's
-// vx0 + K is even).  KAHAN: compensated sums; the accumulators and their corrections fill the
-// registers of 4 columns, so the frames stream twice, 4 columns per pass.
+// vx0 + K is even).  KAHAN: blocked compensated sums -- each stage's FB
+// frames are summed plainly into a partial, which is then added to the
+// running sum with Kahan compensation; partial, sum and correction fill the
+// registers of 4 columns three times over, so the frames stream twice, 4
+// columns per pass.
 template <int PREC, bool VCH, bool KAHAN>
 __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __restrict__ spec, int F,
                                             float2* __restrict__ B, int tile, int sl, float2* __restrict__ S) {
@@ -295,14 +292,18 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
         for (int pass = 0; pass < NP; ++pass) {
             const int col0 = pass * NC;
             const unsigned pm = (kkmask >> col0) & ((1u << NC) - 1u);
-            float2 acc[4][NC];
-            float2 comp[4][KAHAN ? NC : 1];
+            float2 acc[4][NC];                         // the sums (KAHAN: the running sums)
+            float2 part[4][KAHAN ? NC : 1];            // KAHAN: this stage's plain partial sums
+            float2 comp[4][KAHAN ? NC : 1];            // KAHAN: the running sums' corrections
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
 #pragma unroll
                 for (int k = 0; k < NC; ++k) acc[j][k] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k < (KAHAN ? NC : 1); ++k) comp[j][k] = make_float2(0.f, 0.f);
+                for (int k = 0; k < (KAHAN ? NC : 1); ++k) {
+                    comp[j][k] = make_float2(0.f, 0.f);
+                    part[j][k] = make_float2(0.f, 0.f);
+                }
             }
             if (pass > 0) __syncthreads();             // the previous pass is done with the ring
             // Half precision converts stage st + 1 while stage st is
@@ -337,14 +338,28 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
                     Sst = reinterpret_cast<const float2*>(ring) + (st & 1) * FB * BUF;
                 }
                 if (!pm) continue;
+                auto& dst = [&]() -> float2 (&)[4][NC] {
+                    if constexpr (KAHAN) return part; else return acc;
+                }();
                 if (pm == (1u << NC) - 1u) {
 #pragma unroll
                     for (int ff = 0; ff < FB; ++ff)
-                        accumulate_frame<true, NC, KAHAN>(Sst + ff * BUF, wyl, gx, warp, pm, col0, acc, comp);
+                        accumulate_frame<true, NC>(Sst + ff * BUF, wyl, gx, warp, pm, col0, dst);
                 } else {
 #pragma unroll 1
                     for (int ff = 0; ff < FB; ++ff)
-                        accumulate_frame<false, NC, KAHAN>(Sst + ff * BUF, wyl, gx, warp, pm, col0, acc, comp);
+                        accumulate_frame<false, NC>(Sst + ff * BUF, wyl, gx, warp, pm, col0, dst);
+                }
+                if constexpr (KAHAN) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int k = 0; k < NC; ++k)
+                            if (pm & (1u << k)) {                   // warp-uniform
+                                kahan_add(acc[j][k].x, comp[j][k].x, part[j][k].x);
+                                kahan_add(acc[j][k].y, comp[j][k].y, part[j][k].y);
+                                part[j][k] = make_float2(0.f, 0.f);
+                            }
                 }
             }
             asm volatile("cp.async.wait_group 0;");

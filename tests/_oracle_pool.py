@@ -83,3 +83,22 @@ def subfield_whole(task) -> dict:
     np.save(os.path.join(outdir, f"B_{s}.npy"), Bw)
     return {"s": s, "P": P, "M": M, "noise": noise, "A": A, "z": z, "rec": rec,
             "flux": flux, "mu": mu}
+
+
+def subfield_image(task) -> tuple:
+    """Oracle sub-image of one subfield with the given STF (the steps of
+    ``subfield_whole`` on the used pairs, keeping only the image)."""
+    from oracle import speckle_oracle as O
+    path, s, sub, N, fc, R, taper, stf = task
+    frames = np.load(path, mmap_mode="r")
+    In, flux, mu = O.frame_spectra(frames, sub, N, taper)
+    P, M = O.power_mean(In)
+    A = O.amplitude(P, O.noise_floor(P, N, fc), stf, N, fc)
+    wv = used_pairs(N, R, fc)
+    u = wv[:, :2] - wv[:, 2:]
+    Bw = O.bispectrum(In, np.concatenate([u, wv[:, 2:]], 1))
+    up = O.in_half_plane(u[:, 0], u[:, 1])
+    pairs = np.where(up[:, None], np.concatenate([u, wv[:, 2:]], 1), -np.concatenate([u, wv[:, 2:]], 1))
+    z = O.phase_recursion(np.where(up, Bw, np.conj(Bw)), pairs, M, N, fc, R)
+    rec = O.inverse(A, z, float(flux.mean()), float(mu.mean()), O.window2d(sub[2], sub[3], taper))
+    return s, rec
