@@ -63,7 +63,7 @@ extern "C" {
 
 #define SM_ACC_PLAIN 0    /* bispectrum sums: FP32, one rounding per frame    */
 #define SM_ACC_KAHAN 1    /* bispectrum sums: FP32, blocked compensated: each
-                           * group of 4 frames summed plainly, the group sums
+                           * group of 8 frames summed plainly, the group sums
                            * added with Kahan compensation; each subfield
                            * streams its frames twice (half of the offsets
                            * per pass)                                        */

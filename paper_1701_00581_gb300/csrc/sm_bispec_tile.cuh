@@ -187,11 +187,11 @@ __device__ __forceinline__ void chunk_copy(const PlanDev& p, int c, int wx0, int
 // B[sl][tile]; S is the CTA's staging ring of 2 * FB * BUF float2 (16-byte
 // aligned shared memory).  Runs on 128 threads; uses __syncthreads, so the
 // whole CTA must call it.  VCH: V moves in 16-byte chunks (every tile's
-// vx0 + K is even).  KAHAN: blocked compensated sums -- each stage's FB
-// frames are summed plainly into a partial, which is then added to the
-// running sum with Kahan compensation; partial, sum and correction fill the
-// registers of 4 columns three times over, so the frames stream twice, 4
-// columns per pass.
+// vx0 + K is even).  KAHAN: blocked compensated sums -- each block of two
+// stages (2 FB frames) is summed plainly into a partial, which is then added
+// to the running sum with Kahan compensation; partial, sum and correction
+// fill the registers of 4 columns three times over, so the frames stream
+// twice, 4 columns per pass.
 template <int PREC, bool VCH, bool KAHAN>
 __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __restrict__ spec, int F,
                                             float2* __restrict__ B, int tile, int sl, float2* __restrict__ S) {
@@ -293,7 +293,7 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
             const int col0 = pass * NC;
             const unsigned pm = (kkmask >> col0) & ((1u << NC) - 1u);
             float2 acc[4][NC];                         // the sums (KAHAN: the running sums)
-            float2 part[4][KAHAN ? NC : 1];            // KAHAN: this stage's plain partial sums
+            float2 part[4][KAHAN ? NC : 1];            // KAHAN: this block's plain partial sums
             float2 comp[4][KAHAN ? NC : 1];            // KAHAN: the running sums' corrections
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -350,7 +350,9 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
                     for (int ff = 0; ff < FB; ++ff)
                         accumulate_frame<false, NC>(Sst + ff * BUF, wyl, gx, warp, pm, col0, dst);
                 }
-                if constexpr (KAHAN) {
+                // KAHAN: every second stage (8 frames) and after the last one,
+                // the partial sums go into the running sums
+                if constexpr (KAHAN) if ((st & 1) == 1 || st + 1 == nst) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
 #pragma unroll
