@@ -319,7 +319,17 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
         }
         asm volatile("cp.async.wait_group 0;");
         __syncthreads();                          // partials complete, ring r+1 records visible
-        if (more) load_batch(itm, warp, nin);
+        if (more) {
+            load_batch(itm, warp, nin);
+            // the B values of ring r+1's later batches towards L2 while this
+            // ring's points are summed: two 128-byte lines per item
+            for (int e = tid; e < nin; e += PH_THREADS) {
+                if (e < PH_VWARPS * PH_ITEMS && e % PH_VWARPS < PH_WARPS) continue;   // in the first batch
+                const char* a = reinterpret_cast<const char*>(Bs + itm[e].y);
+                asm volatile("prefetch.global.L2 [%0];" :: "l"(a));
+                asm volatile("prefetch.global.L2 [%0];" :: "l"(a + 128));
+            }
+        }
         // (3) one warp per point: sum of its items along a fixed shuffle
         // tree, then z = S / |S|, in T (with T = float GB300's shared FP64
         // unit no longer serialises this step across warps).  The stored
