@@ -396,7 +396,12 @@ int sm_batch_spectra_bispectrum(sm_batch* bt, const sm_batch_io* io, void* strea
 /* The whole path for every burst of the batch: the persistent launch, then
  * per burst P/M/noise, the seeing estimate when io[i].stf is NULL, the
  * modulus (Eq. 1), the photon-noise correction when the channel asks for it,
- * the phase, the inverse transforms and the mosaic.  Asynchronous.         */
+ * the phase, the inverse transforms and the mosaic.  Each burst's stages
+ * after the batched launch run on a stream of the batch's own, forked from
+ * `stream` and joined back to it, so bursts' recursions run side by side;
+ * the call stays asynchronous on `stream` and capturable in a CUDA graph.
+ * SM_EINVAL (before any launch) when a burst has no STF and its seeing
+ * cannot be estimated.                                                      */
 int sm_batch_reconstruct(sm_batch* bt, const sm_batch_io* io, void* stream);
 /* Status of the last run's persistent launch, after the caller has
  * synchronised its stream: SM_OK, or SM_ECUDA when a dependency wait gave up. */

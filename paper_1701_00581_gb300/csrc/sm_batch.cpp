@@ -25,6 +25,11 @@ struct sm_batch {
     int* d_state = nullptr;             // [0] queue head, [1] status, [2..] per-subfield counters
     float2* d_scratch = nullptr;        // per-CTA [K+1][N] transform scratch
     int* h_status = nullptr;            // pinned copy of the status word
+    // each burst's remaining stages run on a stream of their own, forked
+    // from and joined back to the caller's stream by events
+    std::vector<cudaStream_t> side;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
 };
 
 namespace {
@@ -61,6 +66,11 @@ void release(sm_batch* bt) {
     if (bt->d_state) cudaFree(bt->d_state);
     if (bt->d_scratch) cudaFree(bt->d_scratch);
     if (bt->h_status) cudaFreeHost(bt->h_status);
+    for (cudaStream_t st : bt->side)
+        if (st) cudaStreamDestroy(st);
+    if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
+    for (cudaEvent_t ev : bt->ev_join)
+        if (ev) cudaEventDestroy(ev);
     delete bt;
 }
 
@@ -194,6 +204,14 @@ extern "C" int sm_batch_create(int n, const sm_plan* const* plans, const int* F,
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&bt->h_status, sizeof(int), cudaHostAllocDefault);
     if (e != cudaSuccess) return fail(e, "allocating the batch queue");
     *bt->h_status = 0;
+    bt->side.assign(n, nullptr);
+    bt->ev_join.assign(n, nullptr);
+    e = cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&bt->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->ev_join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail(e, "creating the batch's streams");
     cudaSetDevice(old);
     *out = bt;
     return SM_OK;
@@ -314,31 +332,56 @@ extern "C" int sm_batch_status(const sm_batch* bt) {
 }
 
 extern "C" int sm_batch_reconstruct(sm_batch* bt, const sm_batch_io* io, void* stream) {
+    if (!bt || !io) { set_error("NULL argument"); return SM_EINVAL; }
+    for (int i = 0; i < bt->n; ++i) {
+        if (!io[i].stf && (bt->plans[i]->dev.n_cubes < 1 || bt->F[i] < 2)) {
+            set_error("no STF given and the seeing cannot be estimated (needs a cube and F >= 2)");
+            return SM_EINVAL;
+        }
+    }
     int rc = sm_batch_spectra_bispectrum(bt, io, stream);
     if (rc) return rc;
-    for (int i = 0; i < bt->n && !rc; ++i) {
+    // Each burst's remaining stages (statistics, seeing, modulus, phase,
+    // inverse, mosaic) on its own stream, forked from the caller's stream
+    // after the batched launch and joined back to it: small bursts, whose
+    // phase recursion is a handful of CTAs, then run side by side.  The
+    // fork and join are stream-ordered, so the whole call can be captured.
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaEventRecord(bt->ev_fork, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    int forked = 0;
+    for (; forked < bt->n; ++forked) {
+        e = cudaStreamWaitEvent(bt->side[forked], bt->ev_fork, 0);
+        if (e != cudaSuccess) break;
+    }
+    for (int i = 0; i < forked && !rc; ++i) {
         const sm_plan* p = bt->plans[i];
         const sm_batch_io& b = io[i];
+        void* si = bt->side[i];
         const int F = bt->F[i], n = p->dev.n_sub;
         const double* stf = b.stf;
-        rc = sm_stage_stats(p, F, n, b.ws, b.lay, stream);
+        rc = sm_stage_stats(p, F, n, b.ws, b.lay, si);
         if (!rc && !stf) {
-            if (p->dev.n_cubes < 1 || F < 2) {
-                set_error("no STF given and the seeing cannot be estimated (needs a cube and F >= 2)");
-                return SM_EINVAL;
-            }
-            rc = sm_stage_seeing(p, F, 0, n, b.ws, b.lay, stream);
-            if (!rc) rc = sm_stage_seeing_stf(p, b.ws, b.lay, stream);
+            rc = sm_stage_seeing(p, F, 0, n, b.ws, b.lay, si);
+            if (!rc) rc = sm_stage_seeing_stf(p, b.ws, b.lay, si);
             stf = at<double>(b.ws, b.lay->stf);
         }
-        if (!rc) rc = sm_stage_amplitude(p, n, stf, b.ws, b.lay, stream);
+        if (!rc) rc = sm_stage_amplitude(p, n, stf, b.ws, b.lay, si);
         if (!rc && p->dev.photon_gain > 0.0)
             rc = ret(smk::launch_unbias(p->dev, F, n, at<float>(b.ws, b.lay->flux), at<float>(b.ws, b.lay->P),
-                                        at<float2>(b.ws, b.lay->B), static_cast<cudaStream_t>(stream)),
+                                        at<float2>(b.ws, b.lay->B), bt->side[i]),
                      "photon-noise bias kernel");
-        if (!rc) rc = sm_stage_phase(p, n, b.ws, b.lay, stream);
-        if (!rc) rc = sm_stage_inverse(p, F, 0, n, b.ws, b.lay, stream);
-        if (!rc) rc = sm_stage_mosaic(p, b.ws, b.lay, b.out, b.valid, stream);
+        if (!rc) rc = sm_stage_phase(p, n, b.ws, b.lay, si);
+        if (!rc) rc = sm_stage_inverse(p, F, 0, n, b.ws, b.lay, si);
+        if (!rc) rc = sm_stage_mosaic(p, b.ws, b.lay, b.out, b.valid, si);
     }
-    return rc;
+    // join every forked stream, whatever happened above
+    for (int i = 0; i < forked; ++i) {
+        cudaError_t j = cudaEventRecord(bt->ev_join[i], bt->side[i]);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(st, bt->ev_join[i], 0);
+        if (j != cudaSuccess && e == cudaSuccess) e = j;
+    }
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "forking the bursts' streams");
+    return SM_OK;
 }
