@@ -377,7 +377,11 @@ typedef struct {
  * SM_BATCH_GRID launch needs no queue.  opts may be NULL
  * (all tuned).  Allocates the queue, the dependency counters and a
  * transform scratch tile per persistent CTA on the device (sm_batch_info
- * reports the bytes); SM_EINVAL on a bad batch.                             */
+ * reports the bytes), and one stream per burst for the stages after the
+ * batched launch; SM_EINVAL on a bad batch.  A batch serves one run at a
+ * time: its queue, counters and status word are reused by every run, so
+ * runs issued on different streams must be ordered by the caller (runs on
+ * one stream are).                                                          */
 int sm_batch_create(int n, const sm_plan* const* plans, const int* F, const int* frame_type,
                     const sm_batch_opts* opts, sm_batch** out);
 /* The shape the batch was built with (the tuned values filled in).         */
