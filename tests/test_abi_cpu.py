@@ -40,7 +40,20 @@ def test_binding_covers_header():
     assert sorted(_lib.SIGNATURES) == _header_functions()
 
 
-_STRUCTS = ["sm_channel", "sm_plan_info", "sm_workspace_layout", "sm_config", "sm_burst", "sm_result"]
+_STRUCTS = ["sm_channel", "sm_plan_info", "sm_workspace_layout", "sm_config", "sm_burst", "sm_result",
+            "sm_batch_opts", "sm_batch_io"]
+
+
+def test_header_constants_match_binding():
+    """Every integer #define SM_... of the header has the same value in the
+    binding (a constant renumbered on one side only would pass other tests)."""
+    from paper_1701_00581_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "speckle.h")).read()
+    defs = dict(re.findall(r"^#define\s+(SM_[A-Z0-9_]+)\s+(-?\d+)\b", src, flags=re.M))
+    assert len(defs) >= 20
+    for name, value in defs.items():
+        assert hasattr(_lib, name), f"{name} defined in speckle.h but missing from the binding"
+        assert getattr(_lib, name) == int(value), name
 
 
 def test_struct_layouts_match_header(tmp_path):
