@@ -13,8 +13,8 @@ struct TuneEntry {
 
 // BEGIN TABLE (autotune.py)
 constexpr TuneEntry kTune[] = {
-    {256, 24, 2, 4, 3, 1, 109.343},
-    {128, 16, 4, 4, 1, 2, 14.549},
+    {256, 24, 2, 4, 3, 1, 110.061},
+    {128, 16, 2, 4, 3, 1, 14.244},
 };
 // END TABLE
 
