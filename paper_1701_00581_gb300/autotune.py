@@ -36,16 +36,20 @@ ROOT = os.path.dirname(PKG)
 TUNE_H = os.path.join(PKG, "csrc", "sm_tune.h")
 REPORT = os.path.join(ROOT, "profiles", "autotune_batch_launch.md")
 
-# (workload name, synth config, N, R)
-SHAPES = [("tio2560", "tio2560", 256, 24), ("halpha1024", "halpha1024", 128, 16)]
+# (workload name, synth config, N, R, bursts per launch: None = --bursts);
+# single-subfield bursts are timed eight to a launch, the use batching has
+# for them
+SHAPES = [("tio2560", "tio2560", 256, 24, None), ("halpha1024", "halpha1024", 128, 16, None),
+          ("subfield64", "subfield64", 64, 8, 8)]
 LAUNCH_NAMES = {1: "fused persistent", 2: "stage FFT + persistent tiles", 3: "stage FFT + tile grid"}
 GRID = {"lookahead": (2, 4), "ctas_per_sm": (3, 4), "launch": (1, 2, 3), "tile_order": (1, 2)}
 
 
 def tune_shape(torch, cfg, N, R, bursts, reps, frames_n):
-    from paper_1701_00581_gb300 import SM_U16, Batch, Channel, Plan
+    from paper_1701_00581_gb300 import SM_F32, SM_U16, Batch, Channel, Plan
     from synth import CONFIGS, make_burst
     spec = CONFIGS[cfg]
+    ftype = SM_U16 if spec.counts else SM_F32
     F = spec.F if frames_n is None else frames_n
     b = make_burst(spec, channel=3, burst=0, device="cuda:0", F=F)
     plan = Plan(Channel(W=spec.W, H=spec.H, N=N, R=R, max_frames=F))
@@ -63,7 +67,7 @@ def tune_shape(torch, cfg, N, R, bursts, reps, frames_n):
             continue                     # lookahead only orders transform items
         if fuse == 3 and (cps != 4 or order != 1):
             continue                     # the grid launch has no queue: 4 CTAs per SM, the plan's order
-        bt = Batch([plan] * bursts, [F] * bursts, [SM_U16] * bursts, lookahead=la, ctas_per_sm=cps, launch=fuse,
+        bt = Batch([plan] * bursts, [F] * bursts, [ftype] * bursts, lookahead=la, ctas_per_sm=cps, launch=fuse,
                    tile_order=order)
         bt.spectra_bispectrum(items, stream)
         torch.cuda.synchronize()
@@ -96,7 +100,7 @@ def tune_shape(torch, cfg, N, R, bursts, reps, frames_n):
     torch.cuda.empty_cache()
     used = plan.info["n_pairs"] / (plan.info["n_tiles"] * plan.info["tile_pairs"])
     return rows, {"W": spec.W, "H": spec.H, "F": F, "n_sub": n, "n_tiles": plan.info["n_tiles"],
-                  "used_over_slots": used, "stage_ms": stage_ms}
+                  "used_over_slots": used, "stage_ms": stage_ms, "bursts": bursts}
 
 
 def write_table(best):
@@ -124,8 +128,8 @@ def main():
     build.build()
     best, report = {}, []
     t0 = time.time()
-    for name, cfg, N, R in SHAPES:
-        rows, meta = tune_shape(torch, cfg, N, R, args.bursts, args.reps, args.frames)
+    for name, cfg, N, R, nb in SHAPES:
+        rows, meta = tune_shape(torch, cfg, N, R, nb or args.bursts, args.reps, args.frames)
         ok = [r for r in rows if r["ok"]]
         win = min(ok, key=lambda r: r["ms_per_burst"])
         best[(N, R)] = win
@@ -133,18 +137,20 @@ def main():
     out = [f"# Autotune of the batched persistent launch\n",
            f"Command: `python -m paper_1701_00581_gb300.autotune --bursts {args.bursts} --reps {args.reps}"
            + (f" --frames {args.frames}" if args.frames else "") + " --write`",
-           f"(spectra + bispectrum launch time per burst, median of {args.reps}, {args.bursts} bursts per launch; "
+           f"(spectra + bispectrum launch time per burst, median of {args.reps}, {args.bursts} bursts per launch "
+           f"unless stated; "
            f"{time.time() - t0:.0f} s)\n"]
     for name, N, R, meta, rows, win in report:
         out.append(f"## {name}: N = {N}, R = {R} ({meta['W']}x{meta['H']}x{meta['F']}, {meta['n_sub']} subfields, "
-                   f"{meta['n_tiles']} tiles per subfield, used pairs / tile slots = {meta['used_over_slots']:.3f})\n")
-        out.append(f"Per-stage spectra + bispectrum kernels for comparison: {meta['stage_ms']:.2f} ms per burst.\n")
+                   f"{meta['n_tiles']} tiles per subfield, used pairs / tile slots = {meta['used_over_slots']:.3f}; "
+                   f"{meta['bursts']} bursts per launch)\n")
+        out.append(f"Per-stage spectra + bispectrum kernels for comparison: {meta['stage_ms']:.4g} ms per burst.\n")
         out.append("| lookahead | CTAs/SM | launch | tile order | ms per burst |")
         out.append("|---|---|---|---|---|")
         for r in sorted(rows, key=lambda r: r["ms_per_burst"]):
             mark = " **(chosen)**" if r is win else ""
             out.append(f"| {r['lookahead']} | {r['ctas_per_sm']} | {LAUNCH_NAMES[r['launch']]} "
-                       f"| {'plan' if r['tile_order'] == 1 else 'costliest first'} | {r['ms_per_burst']:.2f}{mark} |")
+                       f"| {'plan' if r['tile_order'] == 1 else 'costliest first'} | {r['ms_per_burst']:.4g}{mark} |")
         out.append("")
     text = "\n".join(out)
     print(text)

@@ -13,8 +13,9 @@ struct TuneEntry {
 
 // BEGIN TABLE (autotune.py)
 constexpr TuneEntry kTune[] = {
-    {256, 24, 2, 4, 3, 1, 110.061},
-    {128, 16, 2, 4, 3, 1, 14.244},
+    {256, 24, 2, 4, 3, 1, 110.051},
+    {128, 16, 2, 4, 3, 1, 14.249},
+    {64, 8, 2, 4, 3, 1, 0.021},
 };
 // END TABLE
 
