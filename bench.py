@@ -336,8 +336,10 @@ def serve_mixed(local, tio_burst, tio_ch, capacity, steps, mode=2):
 # ---------------------------------------------------------------------------- batched
 def run_batched(torch, plan, frames, spec, F, n_sub, info, args, stream, peak):
     """args.batch bursts (the same synthetic burst in separate workspaces) per
-    step through sm_batch_reconstruct; also the persistent spectra +
-    bispectrum launch alone, timed with CUDA events on the launching stream."""
+    step through sm_batch_reconstruct, captured once in a CUDA graph and
+    replayed; also the batched spectra + bispectrum launch alone, and the
+    same for the fused persistent launch shape; CUDA events on the launching
+    stream."""
     from paper_1701_00581_gb300 import SM_U16, Batch
     nb = args.batch
     items = []
@@ -346,17 +348,35 @@ def run_batched(torch, plan, frames, spec, F, n_sub, info, args, stream, peak):
         out = torch.empty((spec.H, spec.W), dtype=torch.float32, device=frames.device)
         items.append({"frames": frames, "ws": ws, "lay": lay, "out": out})
     bt = Batch([plan] * nb, [F] * nb, [SM_U16] * nb)
-    for _ in range(args.warmup):
-        bt.reconstruct(items, stream)
+
+    def captured(batch):
+        """The batch's whole reconstruction captured once in a CUDA graph (on
+        a side stream), replayed on `stream` for every step."""
+        batch.reconstruct(items, stream)                 # untimed: first launches, attribute setup
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            batch.reconstruct(items, side)
+        torch.cuda.synchronize()
+        return g
+
+    graph = captured(bt)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.replay()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        bt.reconstruct(items, stream)
-    e1.record(stream)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     ok = bt.status() == 0
+    del graph
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0.record(stream)
     for _ in range(args.steps):
@@ -371,22 +391,24 @@ def run_batched(torch, plan, frames, spec, F, n_sub, info, args, stream, peak):
     # device queue), whatever the tuned shape is, timed the same way
     from paper_1701_00581_gb300 import SM_BATCH_FUSED
     bf = Batch([plan] * nb, [F] * nb, [SM_U16] * nb, launch=SM_BATCH_FUSED)
-    bf.reconstruct(items, stream)
-    torch.cuda.synchronize()
+    fgraph = captured(bf)
     f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    f0.record(stream)
-    for _ in range(args.steps):
-        bf.spectra_bispectrum(items, stream)
-    f1.record(stream)
-    for _ in range(args.steps):
-        bf.reconstruct(items, stream)
-    f2.record(stream)
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        for _ in range(args.steps):
+            bf.spectra_bispectrum(items, stream)
+        f1.record(stream)
+        for _ in range(args.steps):
+            fgraph.replay()
+        f2.record(stream)
     torch.cuda.synchronize()
+    del fgraph
     fused = {"launch_ms_per_burst": round(f0.elapsed_time(f1) / (args.steps * nb), 3),
              "bursts_per_s": round(nb * args.steps / (f1.elapsed_time(f2) / 1000.0), 4),
              "items": bf.info["n_items"], "ctas": bf.info["grid"], "opts": dict(bf.opts),
              "status_ok": bf.status() == 0,
-             "note": "SM_BATCH_FUSED: every transform and tile of the batch from one device queue"}
+             "note": "SM_BATCH_FUSED: every transform and tile of the batch from one device queue; the whole "
+                     "batch captured in a CUDA graph and replayed per step"}
     bf.close()
     triples = info["n_pairs"] * F * n_sub * nb
     ach = FLOPS_PER_TRIPLE * triples / (kms / 1000.0) / 1e12
@@ -398,7 +420,8 @@ def run_batched(torch, plan, frames, spec, F, n_sub, info, args, stream, peak):
                                "frac": round(ach / peak, 4),
                                "note": "bispectrum flops only (14 x used triples); the launch also does every FFT"},
            "note": f"{nb} copies of the burst in separate workspaces per batched spectra + bispectrum launch "
-                   "(the autotuned shape), then each burst's remaining stages; inputs resident in HBM"}
+                   "(the autotuned shape), then each burst's remaining stages, the whole batch captured once in a "
+                   "CUDA graph and replayed per step; inputs resident in HBM"}
     del items
     return rec
 
