@@ -208,6 +208,14 @@ __device__ __forceinline__ int load_acquire(const int* a) {
     return v;
 }
 
+// One bispectrum tile as a call of its own, so that its register allocation
+// does not share the persistent loop's live values.
+template <int PREC, bool VCH>
+__device__ __noinline__ void tile_call(const PlanDev& p, const void* spec, int F, float2* B, int tile, int sl,
+                                       float2* S) {
+    smb::bispec_tile<PREC, VCH, false>(p, spec, F, B, tile, sl, S);
+}
+
 // MINB: CTAs per SM the register allocation is sized for (4: 128 registers
 // per thread; 3: 168, so the tile body does not spill).
 template <int PREC, int MINB>
@@ -255,8 +263,8 @@ k_batch(const __grid_constant__ BatchArgs a, const int4* __restrict__ items, int
             if (!s_skip) {
                 float2* S = reinterpret_cast<float2*>(smem);
                 const bool vch = ((b.p.v_org + b.p.K) & 1) == 0;
-                if (vch) smb::bispec_tile<PREC, true, false>(b.p, b.spec, b.F, b.B, it.w, s, S);
-                else smb::bispec_tile<PREC, false, false>(b.p, b.spec, b.F, b.B, it.w, s, S);
+                if (vch) tile_call<PREC, true>(b.p, b.spec, b.F, b.B, it.w, s, S);
+                else tile_call<PREC, false>(b.p, b.spec, b.F, b.B, it.w, s, S);
             }
         }
         __syncthreads();                             // s_next visible, the item's work done
