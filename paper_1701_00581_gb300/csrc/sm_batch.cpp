@@ -93,7 +93,7 @@ extern "C" int sm_batch_create(int n, const sm_plan* const* plans, const int* F,
                 N = plans[i]->dev.N;
                 R = plans[i]->dev.R;
             }
-        const smt::TuneEntry t = smt::tune_for(N, R);
+        const smt::TuneEntry t = smt::tune_for(N, R, opts.launch);
         if (opts.lookahead == 0) opts.lookahead = t.lookahead;
         if (opts.ctas_per_sm == 0) opts.ctas_per_sm = t.ctas_per_sm;
         if (opts.launch == 0) opts.launch = t.launch;
