@@ -13,12 +13,6 @@ using smi::TILE_PAIRS;
 using smi::TILE_V;
 using smi::TILE_W;
 
-
-using smi::PlanDev;
-using smi::TILE_PAIRS;
-using smi::TILE_V;
-using smi::TILE_W;
-
 constexpr int PW = 18;                  // row pitch of W in smem (float2)
 constexpr int PU = 26;                  // row pitch of U in smem (float2)
 constexpr int UR = smi::WBY + smi::VBY - 1;     // 11 rows of U
@@ -139,9 +133,9 @@ __device__ __forceinline__ void accumulate_frame(const float2* __restrict__ Sb, 
 // 2 FB BUF float2 (FP32 ring), or a 2 FB BUF raw ring and 2 FB BUF float2
 // of compute buffers (half precision).
 template <int PREC> struct Staging;
-template <> struct Staging<SM_FP32> { static constexpr bool ASYNC = true; static constexpr int FB = 4, E = 8; };
-template <> struct Staging<SM_FP16> { static constexpr bool ASYNC = true; static constexpr int FB = 4, E = 4; };
-template <> struct Staging<SM_BF16> { static constexpr bool ASYNC = true; static constexpr int FB = 4, E = 4; };
+template <> struct Staging<SM_FP32> { static constexpr int FB = 4, E = 8; };
+template <> struct Staging<SM_FP16> { static constexpr int FB = 4, E = 4; };
+template <> struct Staging<SM_BF16> { static constexpr int FB = 4, E = 4; };
 
 template <int PREC>
 __device__ __forceinline__ float2 raw_to_float2(unsigned w) {
@@ -195,7 +189,6 @@ __device__ __forceinline__ void chunk_copy(const PlanDev& p, int c, int wx0, int
 template <int PREC, bool VCH, bool KAHAN>
 __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __restrict__ spec, int F,
                                             float2* __restrict__ B, int tile, int sl, float2* __restrict__ S) {
-    constexpr bool ASYNC = Staging<PREC>::ASYNC;
     constexpr int FB = Staging<PREC>::FB, E = Staging<PREC>::E;
     constexpr bool RAW = E == 4;                  // half precision: raw ring + FP32 compute buffer
     const int4 T = p.tiles[tile];
@@ -233,145 +226,142 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
                                    acc[j][2 * q + 1].x * sc, acc[j][2 * q + 1].y * sc);
         }
     };
-    if (ASYNC) {
-        // spectrum values as E-byte words: float2, or half2 / bfloat162
-        using Word = typename std::conditional<E == 8, float2, unsigned>::type;
-        const Word* sp = reinterpret_cast<const Word*>(spec) + sbase;
-        const int nst = (F + FB - 1) / FB;
-        // The ring: E-byte slots, 2 stages x FB frames x BUF; the half-
-        // precision compute buffers (2 x FB x BUF float2) follow it.
-        Word* ring = reinterpret_cast<Word*>(S);
-        float2* cbuf = S + FB * BUF;
-        // Copy slots, fixed for the CTA: global source at frame 0, shared
-        // destination in buffer 0 and size (chunk_copy counts 8-byte values).
-        int src, dst, nb0, nb1 = 0;
-        chunk_copy<VCH>(p, tid, wx0, wy0, vx0, vy0, src, dst, nb0);
-        nb0 = nb0 * E / 8;
-        const Word* g0 = sp + src;
-        const unsigned s0 = (unsigned)__cvta_generic_to_shared(ring + dst);
-        const bool v8 = !VCH && warp == 0;                  // warp 0 copies V by single values
-        const int c1 = VCH ? tid + THREADS : tid + THREADS - NV;
-        const bool has1 = v8 || c1 < NCH_W + NCH_U + (VCH ? NCH_V : 0);
-        if (v8) {
-            const int r = lane >> 3, c = lane & 7;
-            const int i = box_index(p, vx0 + c, vy0 + r);
-            src = i >= 0 ? i : 0; dst = OFF_V + r * smi::VBX + c; nb1 = i >= 0 ? E : 0;
-        } else if (has1) {
-            chunk_copy<VCH>(p, c1, wx0, wy0, vx0, vy0, src, dst, nb1);
-            nb1 = nb1 * E / 8;
-        } else {
-            src = 0; dst = 0;
+    // spectrum values as E-byte words: float2, or half2 / bfloat162
+    using Word = typename std::conditional<E == 8, float2, unsigned>::type;
+    const Word* sp = reinterpret_cast<const Word*>(spec) + sbase;
+    const int nst = (F + FB - 1) / FB;
+    // The ring: E-byte slots, 2 stages x FB frames x BUF; the half-
+    // precision compute buffers (2 x FB x BUF float2) follow it.
+    Word* ring = reinterpret_cast<Word*>(S);
+    float2* cbuf = S + FB * BUF;
+    // Copy slots, fixed for the CTA: global source at frame 0, shared
+    // destination in buffer 0 and size (chunk_copy counts 8-byte values).
+    int src, dst, nb0, nb1 = 0;
+    chunk_copy<VCH>(p, tid, wx0, wy0, vx0, vy0, src, dst, nb0);
+    nb0 = nb0 * E / 8;
+    const Word* g0 = sp + src;
+    const unsigned s0 = (unsigned)__cvta_generic_to_shared(ring + dst);
+    const bool v8 = !VCH && warp == 0;                  // warp 0 copies V by single values
+    const int c1 = VCH ? tid + THREADS : tid + THREADS - NV;
+    const bool has1 = v8 || c1 < NCH_W + NCH_U + (VCH ? NCH_V : 0);
+    if (v8) {
+        const int r = lane >> 3, c = lane & 7;
+        const int i = box_index(p, vx0 + c, vy0 + r);
+        src = i >= 0 ? i : 0; dst = OFF_V + r * smi::VBX + c; nb1 = i >= 0 ? E : 0;
+    } else if (has1) {
+        chunk_copy<VCH>(p, c1, wx0, wy0, vx0, vy0, src, dst, nb1);
+        nb1 = nb1 * E / 8;
+    } else {
+        src = 0; dst = 0;
+    }
+    const Word* g1 = sp + src;
+    const unsigned s1 = (unsigned)__cvta_generic_to_shared(ring + dst);
+    auto copy = [&](unsigned soff, size_t goff, int n0, int n1) {
+        cp_pair<E>(s0 + soff, g0 + goff, n0);
+        if (v8) cp_one<E>(s1 + soff, g1 + goff, n1);
+        else if (has1) cp_pair<E>(s1 + soff, g1 + goff, n1);
+    };
+    // Stage st holds frames FB st .. FB st + FB - 1; frames past F are
+    // zero-filled (no global read) so that every stage is multiplied out whole.
+    auto issue = [&](int st) {
+        if (st < nst) {
+            const unsigned sb = (unsigned)((st & 1) * FB * BUF * E);
+            if (st * FB + FB <= F) {
+#pragma unroll
+                for (int ff = 0; ff < FB; ++ff)
+                    copy(sb + ff * BUF * E, (size_t)(st * FB + ff) * box, nb0, nb1);
+            } else {
+#pragma unroll
+                for (int ff = 0; ff < FB; ++ff) {
+                    const bool in = st * FB + ff < F;
+                    copy(sb + ff * BUF * E, in ? (size_t)(st * FB + ff) * box : 0, in ? nb0 : 0, in ? nb1 : 0);
+                }
+            }
         }
-        const Word* g1 = sp + src;
-        const unsigned s1 = (unsigned)__cvta_generic_to_shared(ring + dst);
-        auto copy = [&](unsigned soff, size_t goff, int n0, int n1) {
-            cp_pair<E>(s0 + soff, g0 + goff, n0);
-            if (v8) cp_one<E>(s1 + soff, g1 + goff, n1);
-            else if (has1) cp_pair<E>(s1 + soff, g1 + goff, n1);
+        asm volatile("cp.async.commit_group;");
+    };
+#pragma unroll
+    for (int pass = 0; pass < NP; ++pass) {
+        const int col0 = pass * NC;
+        const unsigned pm = (kkmask >> col0) & ((1u << NC) - 1u);
+        float2 acc[4][NC];                         // the sums (KAHAN: the running sums)
+        float2 part[4][KAHAN ? NC : 1];            // KAHAN: this block's plain partial sums
+        float2 comp[4][KAHAN ? NC : 1];            // KAHAN: the running sums' corrections
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) acc[j][k] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < (KAHAN ? NC : 1); ++k) {
+                comp[j][k] = make_float2(0.f, 0.f);
+                part[j][k] = make_float2(0.f, 0.f);
+            }
+        }
+        if (pass > 0) __syncthreads();             // the previous pass is done with the ring
+        // Half precision converts stage st + 1 while stage st is
+        // multiplied out, so one barrier per stage serves both: at the
+        // barrier of iteration st the raw stage st + 1 has landed, the
+        // conversion of stage st (into compute buffer st & 1) is complete
+        // and the products of stage st - 1 are done with compute buffer
+        // (st + 1) & 1.  The raw ring slot st & 1 is refilled with stage
+        // st + 2, its conversion having finished before the barrier.
+        auto convert = [&](int st) {
+            const unsigned* rs = reinterpret_cast<const unsigned*>(ring) + (st & 1) * FB * BUF;
+            float2* cb = cbuf + (st & 1) * FB * BUF;
+            for (int e = tid; e < FB * BUF; e += THREADS) cb[e] = raw_to_float2<PREC>(rs[e]);
         };
-        // Stage st holds frames FB st .. FB st + FB - 1; frames past F are
-        // zero-filled (no global read) so that every stage is multiplied out whole.
-        auto issue = [&](int st) {
-            if (st < nst) {
-                const unsigned sb = (unsigned)((st & 1) * FB * BUF * E);
-                if (st * FB + FB <= F) {
-#pragma unroll
-                    for (int ff = 0; ff < FB; ++ff)
-                        copy(sb + ff * BUF * E, (size_t)(st * FB + ff) * box, nb0, nb1);
-                } else {
-#pragma unroll
-                    for (int ff = 0; ff < FB; ++ff) {
-                        const bool in = st * FB + ff < F;
-                        copy(sb + ff * BUF * E, in ? (size_t)(st * FB + ff) * box : 0, in ? nb0 : 0, in ? nb1 : 0);
-                    }
-                }
-            }
-            asm volatile("cp.async.commit_group;");
-        };
-#pragma unroll
-        for (int pass = 0; pass < NP; ++pass) {
-            const int col0 = pass * NC;
-            const unsigned pm = (kkmask >> col0) & ((1u << NC) - 1u);
-            float2 acc[4][NC];                         // the sums (KAHAN: the running sums)
-            float2 part[4][KAHAN ? NC : 1];            // KAHAN: this block's plain partial sums
-            float2 comp[4][KAHAN ? NC : 1];            // KAHAN: the running sums' corrections
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                for (int k = 0; k < NC; ++k) acc[j][k] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int k = 0; k < (KAHAN ? NC : 1); ++k) {
-                    comp[j][k] = make_float2(0.f, 0.f);
-                    part[j][k] = make_float2(0.f, 0.f);
-                }
-            }
-            if (pass > 0) __syncthreads();             // the previous pass is done with the ring
-            // Half precision converts stage st + 1 while stage st is
-            // multiplied out, so one barrier per stage serves both: at the
-            // barrier of iteration st the raw stage st + 1 has landed, the
-            // conversion of stage st (into compute buffer st & 1) is complete
-            // and the products of stage st - 1 are done with compute buffer
-            // (st + 1) & 1.  The raw ring slot st & 1 is refilled with stage
-            // st + 2, its conversion having finished before the barrier.
-            auto convert = [&](int st) {
-                const unsigned* rs = reinterpret_cast<const unsigned*>(ring) + (st & 1) * FB * BUF;
-                float2* cb = cbuf + (st & 1) * FB * BUF;
-                for (int e = tid; e < FB * BUF; e += THREADS) cb[e] = raw_to_float2<PREC>(rs[e]);
-            };
-            issue(0);
-            if constexpr (RAW) {
-                issue(1);
-                asm volatile("cp.async.wait_group 1;");
-                __syncthreads();                      // raw stage 0 visible
-                convert(0);
-            }
-            for (int st = 0; st < nst; ++st) {
-                asm volatile("cp.async.wait_group 0;");
-                __syncthreads();          // stage st visible to all; stage st-1 fully consumed
-                const float2* Sst;
-                if constexpr (RAW) {
-                    issue(st + 2);
-                    if (st + 1 < nst) convert(st + 1);
-                    Sst = cbuf + (st & 1) * FB * BUF;
-                } else {
-                    issue(st + 1);
-                    Sst = reinterpret_cast<const float2*>(ring) + (st & 1) * FB * BUF;
-                }
-                if (!pm) continue;
-                auto& dst = [&]() -> float2 (&)[4][NC] {
-                    if constexpr (KAHAN) return part; else return acc;
-                }();
-                if (pm == (1u << NC) - 1u) {
-#pragma unroll
-                    for (int ff = 0; ff < FB; ++ff)
-                        accumulate_frame<true, NC>(Sst + ff * BUF, wyl, gx, warp, pm, col0, dst);
-                } else {
-#pragma unroll 1
-                    for (int ff = 0; ff < FB; ++ff)
-                        accumulate_frame<false, NC>(Sst + ff * BUF, wyl, gx, warp, pm, col0, dst);
-                }
-                // KAHAN: every second stage (8 frames) and after the last one,
-                // the partial sums go into the running sums
-                if constexpr (KAHAN) if ((st & 1) == 1 || st + 1 == nst) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-#pragma unroll
-                        for (int k = 0; k < NC; ++k)
-                            if (pm & (1u << k)) {                   // warp-uniform
-                                kahan_add(acc[j][k].x, comp[j][k].x, part[j][k].x);
-                                kahan_add(acc[j][k].y, comp[j][k].y, part[j][k].y);
-                                part[j][k] = make_float2(0.f, 0.f);
-                            }
-                }
-            }
+        issue(0);
+        if constexpr (RAW) {
+            issue(1);
+            asm volatile("cp.async.wait_group 1;");
+            __syncthreads();                      // raw stage 0 visible
+            convert(0);
+        }
+        for (int st = 0; st < nst; ++st) {
             asm volatile("cp.async.wait_group 0;");
-            if (pm) write_out(col0, acc);
+            __syncthreads();          // stage st visible to all; stage st-1 fully consumed
+            const float2* Sst;
+            if constexpr (RAW) {
+                issue(st + 2);
+                if (st + 1 < nst) convert(st + 1);
+                Sst = cbuf + (st & 1) * FB * BUF;
+            } else {
+                issue(st + 1);
+                Sst = reinterpret_cast<const float2*>(ring) + (st & 1) * FB * BUF;
+            }
+            if (!pm) continue;
+            auto& dst = [&]() -> float2 (&)[4][NC] {
+                if constexpr (KAHAN) return part; else return acc;
+            }();
+            if (pm == (1u << NC) - 1u) {
+#pragma unroll
+                for (int ff = 0; ff < FB; ++ff)
+                    accumulate_frame<true, NC>(Sst + ff * BUF, wyl, gx, warp, pm, col0, dst);
+            } else {
+#pragma unroll 1
+                for (int ff = 0; ff < FB; ++ff)
+                    accumulate_frame<false, NC>(Sst + ff * BUF, wyl, gx, warp, pm, col0, dst);
+            }
+            // KAHAN: every second stage (8 frames) and after the last one,
+            // the partial sums go into the running sums
+            if constexpr (KAHAN) if ((st & 1) == 1 || st + 1 == nst) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int k = 0; k < NC; ++k)
+                        if (pm & (1u << k)) {                   // warp-uniform
+                            kahan_add(acc[j][k].x, comp[j][k].x, part[j][k].x);
+                            kahan_add(acc[j][k].y, comp[j][k].y, part[j][k].y);
+                            part[j][k] = make_float2(0.f, 0.f);
+                        }
+            }
         }
+        asm volatile("cp.async.wait_group 0;");
+        if (pm) write_out(col0, acc);
     }
 }
 
 
-template <int PREC> __host__ __device__ constexpr int staging_frames() { return Staging<PREC>::FB; }
 // float2 elements of the staging area bispec_tile<PREC> takes
 template <int PREC> __host__ __device__ constexpr int staging_float2() {
     return Staging<PREC>::E == 8 ? 2 * Staging<PREC>::FB * BUF : 3 * Staging<PREC>::FB * BUF;
