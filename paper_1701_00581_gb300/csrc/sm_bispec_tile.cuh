@@ -196,18 +196,15 @@ __device__ __forceinline__ void bispec_tile(const PlanDev& p, const void* __rest
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int wyl = lane >> 2, gx = lane & 3;
 
-    // Offset columns kk for which some lane of this warp owns a used pair:
-    // a warp-uniform mask, so the warp skips columns (and whole tiles) it
-    // does not need without diverging.
+    // Offset columns kk for which some lane of this warp owns a used pair
+    // (from the plan), rebuilt from warp votes so that the compiler treats
+    // the mask as warp-uniform: the warp skips columns (and whole tiles) it
+    // does not need with uniform branches.
+    const unsigned planned = (__ldg(p.tile_masks + tile) >> (8 * warp)) & 0xFFu;
     unsigned kkmask = 0;
 #pragma unroll
-    for (int kk = 0; kk < smi::VBX; ++kk) {
-        bool mine = false;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            mine |= pair_used(wx0 + 4 * gx + j, wy0 + wyl, vx0 + kk, vy0 + warp, p.r2i, p.R * p.R);
-        if (__any_sync(0xffffffffu, mine)) kkmask |= 1u << kk;
-    }
+    for (int kk = 0; kk < smi::VBX; ++kk)
+        if (__any_sync(0xffffffffu, (planned >> kk) & 1u)) kkmask |= 1u << kk;
 
     constexpr int NP = KAHAN ? 2 : 1;                // passes over the frames
     constexpr int NC = smi::VBX / NP;                // offset columns per pass

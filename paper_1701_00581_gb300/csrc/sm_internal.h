@@ -57,6 +57,8 @@ struct PlanDev {
     const float2* winft;     // [n_sub][K+1] DFT of the x window at kx = 0..K
     const float2* tw;        // [N] exp(-2 pi i k / N)
     const int4* tiles;       // [n_tiles] wx0, wy0, vx0, vy0
+    const unsigned* tile_masks;  // [n_tiles] byte q (offset row q, one warp of a tile's CTA): bit e
+                                 //   set when column e holds a used pair of some target
     const int* ring_start;   // [n_rings + 1]
     const int2* points;      // [n_points] (wx, wy), ring-ordered
     const int* wb_start;     // [n_wbx * n_wby + 1] CSR: tiles of each w-block

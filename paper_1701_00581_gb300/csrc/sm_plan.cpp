@@ -212,16 +212,23 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
             for (int vby = 0; vby < pl->n_vby; ++vby)
                 for (int vbx = 0; vbx < pl->n_vbx; ++vbx) {
                     const int vx0 = d.v_org + VBX * vbx, vy0 = -R + VBY * vby;
+                    // used pairs of the tile, and per offset row c (one warp
+                    // of the bispectrum CTA) the columns e holding one
                     long long cnt = 0;
+                    unsigned mask = 0;
                     for (int a = 0; a < WBY; ++a)
                         for (int b = 0; b < WBX; ++b)
                             for (int c = 0; c < VBY; ++c)
                                 for (int e = 0; e < VBX; ++e)
-                                    cnt += pair_used_host(wx0 + b, wy0 + a, vx0 + e, vy0 + c, r2i, R * R);
+                                    if (pair_used_host(wx0 + b, wy0 + a, vx0 + e, vy0 + c, r2i, R * R)) {
+                                        ++cnt;
+                                        mask |= 1u << (8 * c + e);
+                                    }
                     if (cnt == 0) continue;
                     npairs += cnt;
                     pl->tile_of[(size_t)wb * nvb + vby * pl->n_vbx + vbx] = (int)pl->tiles.size();
                     pl->tiles.push_back(make_int4(wx0, wy0, vx0, vy0));
+                    pl->tile_masks.push_back(mask);
                     wb_count[wb]++;
                 }
         }
@@ -420,6 +427,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
         {pl->ann_idx.data(), pl->ann_idx.size() * sizeof(int), 0},
         {pl->ref_start.data(), pl->ref_start.size() * sizeof(int), 0},
         {pl->ref_idx.data(), pl->ref_idx.size() * sizeof(int), 0},
+        {pl->tile_masks.data(), pl->tile_masks.size() * sizeof(unsigned), 0},
     };
     size_t total = 0;
     for (auto& p : pcs) { p.off = total; total += align256(std::max<size_t>(p.bytes, 1)); }
@@ -454,6 +462,7 @@ extern "C" int sm_plan_create(const sm_channel* ch, int device, sm_plan** out) {
     d.ann_idx = (const int*)at(18);
     d.ref_start = (const int*)at(19);
     d.ref_idx = (const int*)at(20);
+    d.tile_masks = (const unsigned*)at(21);
     *out = pl;
     return SM_OK;
 }

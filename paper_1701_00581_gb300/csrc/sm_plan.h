@@ -12,6 +12,7 @@ struct sm_plan {
     smi::PlanDev dev;
     std::vector<int4> subs;
     std::vector<int4> tiles;
+    std::vector<unsigned> tile_masks;   // [tile] byte q: offset columns of row q holding a used pair
     std::vector<int> tile_of;        // [w-block][v-block] -> tile id or -1
     int n_vbx = 0, n_vby = 0;
     std::vector<int> wb_start, wb_tiles;
