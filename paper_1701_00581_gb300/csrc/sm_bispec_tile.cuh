@@ -46,13 +46,6 @@ static_assert(smi::WBX % 2 == 0, "targets start at even box columns");
 // mod 8, distinct.  Differences: slot 13 row + 2 gx + q, rows of lanes 0..7
 // differ by 1 -> {0,2,4,6} + {0,5} mod 8, distinct.  Offsets: broadcast.
 
-__device__ __forceinline__ bool pair_used(int wx, int wy, int vx, int vy, int r2i, int R2) {
-    const int w2 = wx * wx + wy * wy, v2 = vx * vx + vy * vy;
-    const int ux = wx - vx, uy = wy - vy, u2 = ux * ux + uy * uy;
-    const bool inH = wy > 0 || (wy == 0 && wx > 0);
-    return inH && w2 >= 2 && w2 <= r2i && v2 > 0 && v2 <= R2 && v2 < w2 && u2 < w2;
-}
-
 // Asynchronous copies global -> shared of 8 or 16 bytes; the first `bytes`
 // bytes come from global memory, the rest of the copy is zero-filled.
 __device__ __forceinline__ void cp_async8(unsigned smem_addr, const void* gmem, int bytes) {
@@ -178,8 +171,9 @@ __device__ __forceinline__ void chunk_copy(const PlanDev& p, int c, int wx0, int
 }
 
 // One tile (blockIdx-free) of subfield slot `sl`: B of spec[sl] into
-// B[sl][tile]; S is the CTA's staging ring of 2 * FB * BUF float2 (16-byte
-// aligned shared memory).  Runs on 128 threads; uses __syncthreads, so the
+// B[sl][tile]; S is the CTA's staging area, staging_float2<PREC>() float2 of
+// 16-byte aligned shared memory (2 FB BUF for FP32 spectra, 3 FB BUF for
+// half precision).  Runs on 128 threads; uses __syncthreads, so the
 // whole CTA must call it.  VCH: V moves in 16-byte chunks (every tile's
 // vx0 + K is even).  KAHAN: blocked compensated sums -- each block of two
 // stages (2 FB frames) is summed plainly into a partial, which is then added
