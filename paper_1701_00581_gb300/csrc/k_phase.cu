@@ -185,7 +185,10 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
     T2* zs = reinterpret_cast<T2*>(smem + o_zs);
     int4* const itm = reinterpret_cast<int4*>(smem + o_itm);
     int4* const prc = reinterpret_cast<int4*>(smem + o_prc);
-    const int sl = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the warp index through a warp reduction, so that the compiler knows it
+    // is the same in every lane and keeps the loops over it uniform
+    const int sl = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int warp = (int)__reduce_or_sync(0xffffffffu, (unsigned)(tid >> 5));
     double2* zo = z + (size_t)sl * hb;
     for (int e = tid; e < (int)hb; e += PH_THREADS) zs[e] = Cx<T>::make(0, 0);
     __syncthreads();
@@ -252,7 +255,9 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
     // FP32 partial per item; barrier; (2) load ring r+1's first batch from the
     // staged records (its B loads overlap step 3); (3) one warp per point sums
     // its items and stores z = S / |S|; barrier.
-    int i0 = p.ring_items[0], ni = p.ring_items[1] - i0, np = p.ring_start[1] - p.ring_start[0];
+    int i0 = p.ring_items[0];
+    int ni = (int)__reduce_or_sync(0xffffffffu, (unsigned)(p.ring_items[1] - i0));
+    int np = (int)__reduce_or_sync(0xffffffffu, (unsigned)(p.ring_start[1] - p.ring_start[0]));
     stage(0);
     asm volatile("cp.async.wait_group 0;");
     __syncthreads();                              // anchors and ring 0 records visible
@@ -261,8 +266,9 @@ k_phase(PlanDev p, const float2* __restrict__ B, const float2* __restrict__ M, c
     for (int r = 0; r < p.n_rings; ++r) {
         const bool more = r + 1 < p.n_rings;
         const int i0n = more ? p.ring_items[r + 1] : 0;
-        const int nin = more ? p.ring_items[r + 2] - i0n : 0;
-        const int npn = more ? p.ring_start[r + 2] - p.ring_start[r + 1] : 0;
+        const int nin = (int)__reduce_or_sync(0xffffffffu, (unsigned)(more ? p.ring_items[r + 2] - i0n : 0));
+        const int npn = (int)__reduce_or_sync(0xffffffffu,
+                                              (unsigned)(more ? p.ring_start[r + 2] - p.ring_start[r + 1] : 0));
         stage(r + 1);
         // (1) items: products in T, one term per lane, item sums in T
         // One batch of up to PH_ITEMS items of a (virtual) warp: 512 threads
