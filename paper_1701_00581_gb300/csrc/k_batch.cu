@@ -230,10 +230,17 @@ k_batch(const __grid_constant__ BatchArgs a, const int4* __restrict__ items, int
     // of them, so the current index is re-read from shared memory.
     for (;;) {
         __syncthreads();                             // s_cur visible; smem free for the next item
-        const int cur = s_cur;
+        // the item index and record through warp reductions: the same in
+        // every lane, and known so to the compiler, which keeps the item's
+        // dispatch and loops uniform
+        const int cur = (int)__reduce_or_sync(0xffffffffu, (unsigned)s_cur);
         if (cur >= n_items) break;
         if (tid == 0) s_next = atomicAdd(head, 1);   // the next item, fetched while this one runs
-        const int4 it = items[cur];
+        const int4 rec = items[cur];
+        const int4 it = make_int4((int)__reduce_or_sync(0xffffffffu, (unsigned)rec.x),
+                                  (int)__reduce_or_sync(0xffffffffu, (unsigned)rec.y),
+                                  (int)__reduce_or_sync(0xffffffffu, (unsigned)rec.z),
+                                  (int)__reduce_or_sync(0xffffffffu, (unsigned)rec.w));
         const BatchBurst& b = a.b[it.y];
         const int s = it.z;
         if (it.x == 0) {

@@ -14,15 +14,15 @@ struct TuneEntry {
 
 // BEGIN TABLE (autotune.py)
 constexpr TuneEntry kTune[] = {
-    {256, 24, 4, 4, 1, 1, 112.7839},
-    {256, 24, 2, 4, 2, 1, 111.3255},
-    {256, 24, 2, 4, 3, 1, 110.0708},
-    {128, 16, 4, 4, 1, 2, 14.4735},
-    {128, 16, 2, 4, 2, 2, 14.4924},
-    {128, 16, 2, 4, 3, 1, 14.2472},
-    {64, 8, 4, 3, 1, 1, 0.0250},
-    {64, 8, 2, 3, 2, 2, 0.0221},
-    {64, 8, 2, 4, 3, 1, 0.0210},
+    {256, 24, 4, 4, 1, 1, 109.7350},
+    {256, 24, 2, 4, 2, 1, 108.4027},
+    {256, 24, 2, 4, 3, 1, 108.5971},
+    {128, 16, 4, 4, 1, 2, 14.0166},
+    {128, 16, 2, 4, 2, 2, 14.2122},
+    {128, 16, 2, 4, 3, 1, 14.1201},
+    {64, 8, 4, 3, 1, 1, 0.0238},
+    {64, 8, 2, 3, 2, 2, 0.0218},
+    {64, 8, 2, 4, 3, 1, 0.0209},
 };
 // END TABLE
 

@@ -192,11 +192,14 @@ def test_every_launch_shape_gives_the_same_bursts(torch, bursts, mixed, opts):
     bt.close()
 
 
-def test_grid_launch_equals_the_stage_kernels(torch, bursts, mixed):
-    """With the transforms placed first, the batched tile grid gives bitwise
+@pytest.mark.parametrize("launch", ["grid", "tiles"])
+def test_staged_launches_equal_the_stage_kernels(torch, bursts, launch):
+    """With the transforms placed first (the per-stage spectra kernel), the
+    batched tile grid and the persistent launch of the tiles give bitwise
     the bispectrum of the per-stage kernels, burst by burst."""
-    from paper_1701_00581_gb300 import SM_BATCH_GRID
-    assert mixed["opts"]["launch"] == SM_BATCH_GRID   # the tuned launch of a batch led by N = 256
+    from paper_1701_00581_gb300 import SM_BATCH_GRID, SM_BATCH_TILES
+    opts = {"launch": {"grid": SM_BATCH_GRID, "tiles": SM_BATCH_TILES}[launch]}
+    got = _run(torch, ORDER, bursts, opts)
     for nm in ORDER:
         spec, N, R, given = CASES[nm]
         plan, io = _setup(torch, nm, bursts[nm])
@@ -205,8 +208,8 @@ def test_grid_launch_equals_the_stage_kernels(torch, bursts, mixed):
         plan.stage_bispectrum(spec.F, n, io["ws"], io["lay"])
         torch.cuda.synchronize()
         v = plan.views(io["ws"], io["lay"], spec.F, n)
-        assert np.array_equal(v["spec"].cpu().numpy(), mixed[nm]["spec"])
-        assert np.array_equal(v["B"].cpu().numpy(), mixed[nm]["B"])
+        assert np.array_equal(v["spec"].cpu().numpy(), got[nm]["spec"])
+        assert np.array_equal(v["B"].cpu().numpy(), got[nm]["B"])
 
 
 def test_batch_is_captured_in_a_cuda_graph(torch, bursts, mixed):
