@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--inflight", type=int, default=2, help="bursts in flight on the served e2e path")
     ap.add_argument("--batch", type=int, default=4,
                     help="bursts per batched persistent launch in the batched record (0: skip it)")
+    ap.add_argument("--batch-launch", default="tuned", choices=["tuned", "fused", "tiles", "grid"],
+                    help="launch shape of the batched record's main part (tuned: the autotuned table's)")
     ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2],
                     help="served paths: 0 bursts' kernels in submission order, 1 concurrently, 2 pipelined (a "
                          "burst's phase/inverse/mosaic beside the next burst's transforms and bispectrum)")
@@ -347,7 +349,9 @@ def run_batched(torch, plan, frames, spec, F, n_sub, info, args, stream, peak):
         ws, lay = plan.workspace(F, n_sub)
         out = torch.empty((spec.H, spec.W), dtype=torch.float32, device=frames.device)
         items.append({"frames": frames, "ws": ws, "lay": lay, "out": out})
-    bt = Batch([plan] * nb, [F] * nb, [SM_U16] * nb)
+    from paper_1701_00581_gb300 import SM_BATCH_FUSED, SM_BATCH_GRID, SM_BATCH_TILES
+    launch = {"tuned": 0, "fused": SM_BATCH_FUSED, "tiles": SM_BATCH_TILES, "grid": SM_BATCH_GRID}[args.batch_launch]
+    bt = Batch([plan] * nb, [F] * nb, [SM_U16] * nb, launch=launch)
 
     def captured(batch):
         """The batch's whole reconstruction captured once in a CUDA graph (on
@@ -389,7 +393,6 @@ def run_batched(torch, plan, frames, spec, F, n_sub, info, args, stream, peak):
     bt.close()
     # the persistent fused launch itself (transforms and tiles from one
     # device queue), whatever the tuned shape is, timed the same way
-    from paper_1701_00581_gb300 import SM_BATCH_FUSED
     bf = Batch([plan] * nb, [F] * nb, [SM_U16] * nb, launch=SM_BATCH_FUSED)
     fgraph = captured(bf)
     f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
